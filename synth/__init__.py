@@ -1,0 +1,153 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds only workload descriptions and data simulation: the five
+evaluation workloads (sizes, parameters, HODLR options), the observation vector
+y simulated from the generative model, and the per-dataset draws of the batched
+1-D workload.  It contains none of the hierarchical method's arithmetic
+(no sketching, factorization, likelihood or trace code) and imports neither
+``oracle`` nor the CUDA package.
+
+Data recipe (the paper's own data came from R RandomFields simulations on the
+wind and ADR models, Sec. 5; it is not available, so seeded stand-ins are used):
+  * latent Matern field u ~ N(0, K_u) drawn by circulant embedding of the
+    Matern covariance (Sec. 5.1, eq. whittle covariance) on a (2G)^d torus, with
+    negative embedding eigenvalues clipped to zero;
+  * physics A = -Laplacian_h + kappa^2 on the interior nodes x_i = i/(G+1)
+    with Dirichlet boundary (3-point / 5-point finite differences);
+  * univariate observation y = A^{-1} u + sqrt(tau2) * eps,
+    bivariate observation y = (u, A^{-1} u) + sqrt(tau2) * eps (Sec. 2.1,
+    eq. cov model with the linear map L = [I; A^{-1}]).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.fft
+import scipy.linalg
+
+__all__ = ["Workload", "WORKLOADS", "workload", "simulate_y", "batched_draws",
+           "small_workload"]
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One evaluation workload: model, parameter point and HODLR options."""
+    name: str
+    dim: int            # 1 or 2
+    G: int              # grid points per axis
+    nvar: int           # 1: y = A^{-1}u ; 2: y = (u, A^{-1}u)
+    nu: float           # Matern smoothness, 0.5 or 1.5
+    theta: tuple        # (sigma2, ell, kappa, tau2)
+    leaf: int           # leaf size in matrix rows
+    cap: int            # rank cap (stored factor width)
+    c: int              # probe columns per level sketch
+    tol: float          # relative truncation tolerance (0 = fixed rank)
+    precision: str      # "fp64" | "fp32" | "bf16"
+    seed_probe: int = 1
+    seed_data: int = 0
+
+    @property
+    def n_points(self) -> int:
+        return self.G ** self.dim
+
+    @property
+    def N(self) -> int:
+        return self.nvar * self.n_points
+
+
+WORKLOADS = {
+    # 1-D univariate, FP64 plain method, n = 1024, leaf 64, rank 16 + 8 oversampling.
+    "C0": Workload("C0", 1, 1024, 1, 1.5, (1.0, 0.1, 5.0, 1e-4), 64, 24, 24, 0.0, "fp64"),
+    # 1-D bivariate co-kriging, 2^16 points x 2 variables, leaf 256, rank 32, FP32 bulk.
+    "C1": Workload("C1", 1, 65536, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 256, 32, 32, 0.0, "fp32"),
+    # 2-D univariate 512^2 Morton, nu = 1/2, adaptive rank tol 1e-6 cap 128, leaf 256.
+    "C2": Workload("C2", 2, 512, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32"),
+    # 2-D bivariate 1024^2 (N = 2^21), nu = 3/2, leaf 512, tol 1e-5 cap 192, BF16 sketch.
+    "C4": Workload("C4", 2, 1024, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 512, 192, 200, 1e-5, "bf16"),
+}
+
+
+def workload(name: str) -> Workload:
+    return WORKLOADS[name]
+
+
+def small_workload(dim=1, G=256, nvar=1, nu=1.5, theta=(1.0, 0.1, 5.0, 1e-4), leaf=32,
+                   cap=12, c=12, tol=0.0, precision="fp64", seed_probe=1, seed_data=0,
+                   name="small") -> Workload:
+    """A reduced-size workload of the same structure (for parity tests)."""
+    return Workload(name, dim, G, nvar, nu, tuple(theta), leaf, cap, c, tol, precision,
+                    seed_probe, seed_data)
+
+
+def batched_draws(n_datasets: int = 64, seed: int = 2):
+    """Per-dataset (N_d, ell, kappa) of the batched 1-D workload.
+
+    N_d is uniform on the integers [4096, 65536]; ell and kappa are log-uniform on
+    [0.02, 0.3] and [2, 20]; sigma2 = 1 and tau2 = 1e-4.
+    """
+    rng = np.random.default_rng(seed)
+    n = rng.integers(4096, 65536 + 1, size=n_datasets)
+    ell = np.exp(rng.uniform(math.log(0.02), math.log(0.3), size=n_datasets))
+    kappa = np.exp(rng.uniform(math.log(2.0), math.log(20.0), size=n_datasets))
+    return [(int(n[i]), (1.0, float(ell[i]), float(kappa[i]), 1e-4)) for i in range(n_datasets)]
+
+
+# ----------------------------------------------------------------------------------------
+# data simulation (independent implementation; not used by the estimator)
+
+def _matern_unit(r, ell, nu):
+    z = r / ell
+    if nu == 0.5:
+        return np.exp(-z)
+    if nu == 1.5:
+        return (1.0 + z) * np.exp(-z)
+    raise ValueError("nu must be 0.5 or 1.5")
+
+
+def _sample_latent(dim, G, nu, sigma2, ell, rng):
+    h = 1.0 / (G + 1)
+    L = 2 * G
+    k = np.arange(L)
+    d = np.minimum(k, L - k).astype(np.float64)
+    if dim == 1:
+        emb = sigma2 * _matern_unit(h * d, ell, nu)
+        lam = np.fft.fft(emb).real
+        lam = np.maximum(lam, 0.0)
+        z = rng.standard_normal(L)
+        u = np.fft.ifft(np.sqrt(lam) * np.fft.fft(z)).real
+        return u[:G]
+    dx, dy = np.meshgrid(d, d, indexing="xy")
+    emb = sigma2 * _matern_unit(h * np.sqrt(dx * dx + dy * dy), ell, nu)
+    lam = np.maximum(np.fft.fft2(emb).real, 0.0)
+    z = rng.standard_normal((L, L))
+    u = np.fft.ifft2(np.sqrt(lam) * np.fft.fft2(z)).real
+    return u[:G, :G].reshape(-1)          # natural order: index = iy * G + ix
+
+
+def _solve_A(dim, G, kappa, v):
+    h = 1.0 / (G + 1)
+    if dim == 1:
+        ab = np.zeros((3, G))
+        ab[0, 1:] = -1.0 / h ** 2
+        ab[1, :] = 2.0 / h ** 2 + kappa ** 2
+        ab[2, :-1] = -1.0 / h ** 2
+        return scipy.linalg.solve_banded((1, 1), ab, v)
+    j = np.arange(1, G + 1)
+    lam = 4.0 * np.sin(j * np.pi / (2 * (G + 1))) ** 2 / h ** 2
+    V = scipy.fft.dstn(v.reshape(G, G), type=1, norm="ortho")
+    V = V / (lam[:, None] + lam[None, :] + kappa ** 2)
+    return scipy.fft.idstn(V, type=1, norm="ortho").reshape(-1)
+
+
+def simulate_y(w: Workload, theta=None, seed=None) -> np.ndarray:
+    """Observation vector y in natural order (stacked [y1; y2] when bivariate)."""
+    sigma2, ell, kappa, tau2 = w.theta if theta is None else theta
+    rng = np.random.default_rng(w.seed_data if seed is None else seed)
+    u = _sample_latent(w.dim, w.G, w.nu, sigma2, ell, rng)
+    if w.nvar == 1:
+        clean = _solve_A(w.dim, w.G, kappa, u)
+    else:
+        clean = np.concatenate([u, _solve_A(w.dim, w.G, kappa, u)])
+    return clean + math.sqrt(tau2) * rng.standard_normal(clean.shape[0])
