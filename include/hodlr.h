@@ -1,0 +1,177 @@
+/*
+ * hodlr.h -- C ABI of the GB300 HODLR Gaussian-process likelihood library.
+ *
+ * The library evaluates, for the physics-based covariance of arXiv 2303.10102
+ * (Sec. 2.1, eq. cov model)
+ *     K(theta) = L K_u(theta) L^T + tau2 I,   theta = (sigma2, ell, kappa, tau2),
+ * the negative log-likelihood, its gradient and the expected Fisher information of the
+ * hierarchical (HODLR) approximation K~(theta) (Sec. 4, eq. log-like approximated,
+ * eq. score approximated, eq. fisher info approximated).  K~ is built matrix-free from
+ * products of K with patterned Gaussian probes (Alg. 1, Sec. 3.2.2); the derivative
+ * matrices dK~/dtheta_j are built in the same structure (Alg. 2, Sec. 3.3); K~ is
+ * factorized hierarchically (eq. one way factor, App. C); the traces are exact
+ * (App. B).  Every arithmetic step runs in the library's own CUDA kernels.
+ *
+ * Conventions common to all calls
+ *   - Return value: HODLR_OK (0) or a negative HODLR_E* code.  A failed call leaves its
+ *     outputs untouched; hodlr_last_error() describes the failure; the context stays
+ *     usable.
+ *   - Device memory: the library allocates nothing.  The caller queries the size with
+ *     hodlr_workspace_size() and passes one device buffer to hodlr_create(); the
+ *     buffer stays owned by the caller and must outlive the context.
+ *   - Stream: all device work is ordered on the CUDA stream given to hodlr_create()
+ *     (NULL = legacy default stream).  Calls that return host values synchronise it.
+ *   - theta: host array of 4 doubles (sigma2, ell, kappa, tau2), all > 0.
+ *     hodlr_nll/grad/fisher rebuild K~ when theta differs bitwise from the last build.
+ *   - y: device array of N doubles in natural order (1-D: grid index; 2-D: iy*G + ix;
+ *     bivariate: [y1 (all points); y2 (all points)]).
+ *   - Sign: outputs are the NLL and its gradient g = -S (S = score of eq. score).
+ */
+#ifndef HODLR_H
+#define HODLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HODLR_OK 0
+#define HODLR_EINVAL (-1)    /* bad argument or unsupported combination          */
+#define HODLR_ENOMEM (-2)    /* workspace too small                               */
+#define HODLR_ENOTPD (-3)    /* a leaf or SMW core Cholesky failed (K~ not SPD)   */
+#define HODLR_ENUMERIC (-4)  /* NaN / Inf met in an input or a result             */
+#define HODLR_ETIMEOUT (-5)  /* a bounded device wait gave up                     */
+#define HODLR_ENOTIMPL (-6)  /* feature not built                                 */
+#define HODLR_ECUDA (-7)     /* a CUDA runtime call failed                        */
+
+#define HODLR_FP64 0         /* everything in FP64                                */
+#define HODLR_MIXED_FP32 1   /* FP32 sketch/GEMM bulk; FP64 leaf Cholesky, SMW
+                                cores, log-det and refinement of K~^{-1} y        */
+
+typedef struct hodlr_ctx hodlr_ctx;
+
+/* Model descriptor (copied by hodlr_create).
+ *   dim      1 or 2 (regular grid of G points per axis on (0,1)^dim, h = 1/(G+1))
+ *   grid     {G, G} for dim 2, {G, 1} for dim 1
+ *   nvar     1: y = A^{-1} u   (K = A^{-1} K_u A^{-1} + tau2 I)
+ *            2: y = (u, A^{-1} u)  (K = L K_u L^T + tau2 I, L = [I; A^{-1}])
+ *   nu       Matern smoothness 0.5 or 1.5 (eq. whittle covariance, no sqrt(2 nu))
+ *   precision HODLR_FP64 or HODLR_MIXED_FP32                                      */
+typedef struct {
+  int dim;
+  int grid[2];
+  int nvar;
+  double nu;
+  int precision;
+} hodlr_model;
+
+/* Construction options (Alg. 1 / Sec. 3.2.2 and the readings of the rank rule).
+ *   leaf        leaf block size in matrix rows (multiple of nvar)
+ *   rank_or_cap kept-rank cap per off-diagonal block (stored factor width)
+ *   oversample  probe columns c = rank_or_cap + oversample
+ *   tol         relative truncation tolerance of the pivoted QR (0 = fixed rank);
+ *               a block keeps the leading |R_ii| > max(tol, guard) |R_11|, guard =
+ *               1e-5 (FP64) or 1e-3 (mixed).  The guard bounds cond(R) and with it the
+ *               rounding amplification of the differentiated QR (Alg. 2).
+ *   seed        Philox key of the probes (fixed across theta, Sec. 3.3)            */
+typedef struct {
+  int leaf;
+  int rank_or_cap;
+  int oversample;
+  double tol;
+  uint64_t seed;
+} hodlr_opts;
+
+/* Bytes of device workspace needed by a context for (m, o).  0 on bad arguments. */
+size_t hodlr_workspace_size(const hodlr_model* m, const hodlr_opts* o);
+
+/* Create a context.  workspace: caller-owned device buffer of >= workspace_bytes
+ * bytes, 256-byte aligned.  cuda_stream: a cudaStream_t (may be NULL).  */
+int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, void* cuda_stream,
+                 void* workspace, size_t workspace_bytes);
+
+/* Build K~(theta) and dK~/d theta_j (Alg. 1, Sec. 3.2.2, Alg. 2, Sec. 3.3) and
+ * factorize K~ (eq. one way factor, App. C).  points must be NULL (regular grid). */
+int hodlr_build(hodlr_ctx* h, const double* theta, const double* points);
+
+/* NLL of eq. log-like approximated (negated): N/2 log 2pi + 1/2 log|K~| + 1/2 y^T K~^{-1} y.
+ * nll_out: host double.  */
+int hodlr_nll(hodlr_ctx* h, const double* theta, const double* y, double* nll_out);
+
+/* Gradient of the NLL (eq. score approximated, negated): g_j = 1/2 tr(K~^{-1} K~_j)
+ * - 1/2 a^T K~_j a, a = K~^{-1} y, with the exact trace of App. B.  grad_out: host, 4. */
+int hodlr_grad(hodlr_ctx* h, const double* theta, const double* y, double* grad_out);
+
+/* Expected Fisher information (eq. fisher info approximated):
+ * I_ij = 1/2 tr(K~^{-1} K~_i K~^{-1} K~_j), exact (App. B.2/B.3).  fisher_out: host, 16,
+ * row-major.  */
+int hodlr_fisher(hodlr_ctx* h, const double* theta, double* fisher_out);
+
+/* NLL, gradient and Fisher of one theta in one call (one "evaluation").  Any output
+ * pointer may be NULL.  */
+int hodlr_eval(hodlr_ctx* h, const double* theta, const double* y, double* nll_out,
+               double* grad_out, double* fisher_out);
+
+/* NLL and gradient of nb independent contexts (batched 1-D workload), each with its own
+ * theta (thetas: nb*4 host doubles) and y (ys: nb device pointers).  Outputs: nll_out
+ * [nb], grad_out [nb*4] host.  */
+int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas,
+                         const double* const* ys, double* nll_out, double* grad_out);
+
+/* Tree order: perm_out[position] = natural index (host, N int64).  The ordering is the
+ * KD / Morton order of Sec. 5.2 with the cluster tree of Sec. 3.2.2.  */
+int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out);
+
+/* Sizes: out[0]=N, out[1]=tau (levels), out[2]=leaf size, out[3]=probe columns c,
+ * out[4]=rank cap, out[5]=number of leaves.  */
+int hodlr_dims(const hodlr_ctx* h, int64_t* out);
+
+/* Kept ranks of the last build: ranks_out[(2^(l-1) - 1) + p] for level l, pair p
+ * (host int32, 2^tau - 1 entries).  */
+int hodlr_ranks(const hodlr_ctx* h, int32_t* ranks_out);
+
+/* Pivot sets J of the last build, and freezing.  Layout: per pair (same order as
+ * hodlr_ranks) c int32 entries, the first rank entries are J, the rest -1.
+ * hodlr_set_pivots(h, J) makes subsequent builds use the given sets instead of taking
+ * pivoted QRs (Sec. 3.3: the sampling pattern is held fixed); J = NULL unfreezes.  */
+int hodlr_get_pivots(const hodlr_ctx* h, int32_t* piv_out);
+int hodlr_set_pivots(hodlr_ctx* h, const int32_t* piv_in);
+
+/* Physics product (eq. cov model): Y = K X (which=0) or dK/dtheta_which X (which=1..4
+ * for sigma2, ell, kappa, tau2) at theta, for X (device, N x ncols column-major, FP64,
+ * natural order).  Y: device, same layout.  */
+int hodlr_apply(hodlr_ctx* h, const double* theta, int which, const double* X, double* Y,
+                int ncols);
+
+/* Probe panel R^(level) of the level sketch (Alg. 1 step 1, patterned as in Sec. 3.2.2)
+ * in tree order: out device N x ncols FP64 column-major, ncols <= c.  */
+int hodlr_probe(hodlr_ctx* h, int level, int ncols, double* out);
+
+/* Dense form of K~ (which=0) or K~_j (which=1..4) in tree order, N x N column-major
+ * FP64 device buffer (small N only; for tests).  Needs a prior build.  */
+int hodlr_densify(hodlr_ctx* h, int which, double* out);
+
+/* K~^{-1} b in natural order (device FP64 vectors of length N) and log|K~| (host).  */
+int hodlr_solve(hodlr_ctx* h, const double* b, double* x);
+int hodlr_logdet(hodlr_ctx* h, double* logdet_out);
+
+/* Exact traces (App. B.3): t[i] = tr(K~^{-1} M_i), f[3*i+j] = tr(K~^{-1} M_i K~^{-1} M_j)
+ * for M = (I, K~_ell, K~_kappa).  t: host 3, f: host 9.  */
+int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out);
+
+/* Number of K or K_j vector products (columns) of the last build (Sec. 3.2.2 count).  */
+int hodlr_napply(const hodlr_ctx* h, int64_t* out);
+
+/* Launch statistics: number of kernels launched since the last reset (host int64).  */
+int hodlr_kernel_count(const hodlr_ctx* h, int64_t* out);
+int hodlr_reset_kernel_count(hodlr_ctx* h);
+
+const char* hodlr_last_error(const hodlr_ctx* h);
+void hodlr_destroy(hodlr_ctx* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HODLR_H */

@@ -1,0 +1,41 @@
+// Shared definitions of the HODLR CUDA library (device helpers, launch bookkeeping).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <stdexcept>
+#include <string>
+
+namespace hodlr {
+
+// Error raised inside the library; converted to a return code at the C ABI.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define HODLR_CUDA(call)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::hodlr::Error(-7, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+// Kernel-launch counter (per process); every launcher bumps it.
+extern long long g_kernel_launches;
+inline void count_launch(int n = 1) { g_kernel_launches += n; }
+
+inline void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(-7, std::string(what) + ": " + cudaGetErrorString(e));
+  count_launch();
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+template <class T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+}  // namespace hodlr

@@ -1,0 +1,1336 @@
+// HODLR likelihood engine: context, workspace plan, build / factor / solve / trace
+// orchestration and the C ABI of include/hodlr.h.
+//
+// Data layout (device, column-major panels with leading dimension N, tree order):
+//   F[l]     N x cap  level-l factors: rows of left children hold Q (W), rows of right
+//                     children hold B~ (X), so the pair block is Q B~^T (eq. lowrnkB11).
+//   dF[j][l] N x cap  derivative factors [dQ; dB~] of parameter j (eq. diff low-rank); the
+//                     derivative block is dQ B~^T + Q dB~^T (rank 2w).
+//   U[l]     N x cap  K~_{c1}^{-1} W and K~_{c2}^{-1} X of the factorization (App. C).
+//   CP[l]    per node (2w x 2w): C^{-1} P with C = [[I, Sx],[Sw, I]] the SMW core of the
+//            node (Sw = W^T K~_{c1}^{-1} W, Sx = X^T K~_{c2}^{-1} X) and P the half swap.
+//   leaves   A_b, A_b^{-1} (n_l x n_l), dA_b per derivative parameter.
+// A node v with children c1, c2 factors as K~_v = diag(K~_c1, K~_c2)(I + U V^T) with
+// U = [[W~,0],[0,X~]], V = [[0,W],[X,0]] (eq. one way factor, App. C), so
+//   K~_v^{-1} = (I - U C^{-1} V^T) diag(K~_c1^{-1}, K~_c2^{-1}),
+//   log|K~_v| = log|K~_c1| + log|K~_c2| + log|I - Lw^T Sx Lw|  (Sw = Lw Lw^T, Sylvester).
+// The exact traces of App. B are taken through the same node recursion:
+//   tr(K~^{-1} M) = sum_leaves tr(A_b^{-1} M_b) - sum_nodes tr(CP_v U_v^T M_v U_v),
+// and the four-factor trace adds, per node, the cross term of the two off-diagonal blocks
+// and the C^{-1} corrections (see traces()).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hodlr.h"
+#include "common.cuh"
+#include "ops.h"
+
+namespace hodlr {
+
+// ------------------------------------------------------------------------------ arena
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  bool plan = true;
+  template <class X> X* take(size_t n) {
+    size_t bytes = ((n * sizeof(X) + 255) / 256) * 256;
+    size_t o = off;
+    off += bytes;
+    if (plan) return nullptr;
+    if (off > cap) throw Error(HODLR_ENOMEM, "workspace too small");
+    return (X*)(base + o);
+  }
+};
+
+struct Base {
+  virtual ~Base() {}
+  std::string err;
+  virtual void build(const double* theta) = 0;
+  virtual void eval(const double* theta, const double* y, double* nll, double* grad, double* fisher) = 0;
+  virtual void apply_nat(const double* theta, int which, const double* X, double* Y, int ncols) = 0;
+  virtual void probe(int level, int ncols, double* out) = 0;
+  virtual void densify(int which, double* out) = 0;
+  virtual void solve_nat(const double* b, double* x) = 0;
+  virtual void traces(double* t, double* f) = 0;
+  virtual void set_pivots(const int32_t* piv) = 0;
+  virtual void get_pivots(int32_t* piv) const = 0;
+  int N = 0, tau = 0, leaf = 0, c = 0, cap = 0, nleaves = 0;
+  std::vector<int64_t> perm64;
+  std::vector<std::vector<int>> host_rank;   // per level
+  long long napply = 0;
+  double logdet = 0.0;
+  bool built = false;
+};
+
+static const int NPAR = 4;  // sigma2, ell, kappa, tau2
+
+template <class T>
+struct Engine : Base {
+  using Acc = T;
+  // model / options
+  int dim, G, nvar, prec;
+  double nu, tol, guard;
+  uint64_t seed;
+  int Ns;
+  PhysicsDesc ph;
+  cudaStream_t st;
+  // tree
+  std::vector<std::vector<int>> bnd;     // per depth: node boundaries (2^d + 1)
+  int* d_perm = nullptr;                 // tree position -> natural index (var-major chunk layout)
+  int* d_perm_plain = nullptr;           // tree position -> natural index (plain)
+  std::vector<unsigned char*> d_mask;    // per level (1..tau): right-child rows
+  int* d_leafb = nullptr;
+  // level data
+  std::vector<T*> F, U, CP, dF[2];
+  std::vector<int*> d_rank, d_piv;
+  std::vector<double*> d_nodelog;
+  std::vector<int> w;                    // width per level
+  // leaves
+  T *A = nullptr, *Ainv = nullptr, *dA[2] = {nullptr, nullptr};
+  double* leaflog = nullptr;
+  // physics state
+  T *lam0 = nullptr, *lam1 = nullptr, *tw = nullptr, *Sdst = nullptr;
+  double* coef = nullptr;
+  void* fftw = nullptr;
+  size_t fftw_bytes = 0;
+  int qc = 0;                            // physics column chunk
+  T *nx = nullptr, *na = nullptr, *nb_ = nullptr, *nu_ = nullptr, *nu2 = nullptr, *ns = nullptr, *ne = nullptr,
+    *nt = nullptr, *nw = nullptr;
+  // sketch buffers
+  T *R = nullptr, *KR = nullptr, *KjR[2] = {nullptr, nullptr}, *Y = nullptr, *S = nullptr, *KS = nullptr,
+    *KjS[2] = {nullptr, nullptr}, *dS = nullptr, *KdS = nullptr, *YJ = nullptr, *Q1 = nullptr;
+  double *gram = nullptr, *pwork = nullptr;
+  T *RinvJ = nullptr, *Rinv = nullptr, *Linv_T = nullptr, *sm1 = nullptr, *sm2 = nullptr, *sm3 = nullptr;
+  // factor workspaces (FP64 small)
+  double *sw = nullptr, *sx = nullptr, *lw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *phi = nullptr;
+  // panels for leaves / solves / traces
+  T *E[3] = {nullptr, nullptr, nullptr};
+  T *WP = nullptr, *WZ = nullptr;       // wide panels N x 10 cap
+  T *fg = nullptr, *stb = nullptr;      // solve coefficient blocks
+  T *nodeG = nullptr, *nodeX = nullptr; // per-node 2w x 2w matrices
+  T *tpan = nullptr;                    // peel T blocks
+  double *vec_d = nullptr, *vec_d2 = nullptr, *vec_d3 = nullptr, *red = nullptr, *res = nullptr;
+  T* vec_t = nullptr;
+  double* Afp = nullptr;
+  int* d_status = nullptr;
+  Scratch scratch;
+  // state
+  double theta_built[4] = {0, 0, 0, 0};
+  bool frozen = false;
+  int nwide = 10, wide = 0;
+  double* LinvLeaf = nullptr;
+
+  Engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t s_) {
+    dim = m->dim; G = m->grid[0]; nvar = m->nvar; nu = m->nu; prec = m->precision;
+    leaf = o->leaf; cap = o->rank_or_cap; c = o->rank_or_cap + o->oversample; tol = o->tol; seed = o->seed;
+    guard = prec == HODLR_FP64 ? 1e-5 : 1e-3;
+    st = s_;
+    if (dim < 1 || dim > 2 || nvar < 1 || nvar > 2 || G < 2 || leaf < nvar || leaf % nvar || cap < 1 || c < cap ||
+        (nu != 0.5 && nu != 1.5))
+      throw Error(HODLR_EINVAL, "bad model or options");
+    if (dim == 2 && m->grid[1] != G) throw Error(HODLR_EINVAL, "2-D grids must be square");
+    Ns = dim == 1 ? G : G * G;
+    N = nvar * Ns;
+    // tree (Sec. 3.2.2 index sets; KD / Morton order of Sec. 5.2)
+    int lps = leaf / nvar;
+    tau = 0;
+    while ((Ns + (1 << tau) - 1) / (1 << tau) > lps) ++tau;
+    std::vector<std::vector<int>> sb(tau + 1);
+    sb[0] = {0, Ns};
+    for (int d = 1; d <= tau; ++d) {
+      for (size_t q = 0; q + 1 < sb[d - 1].size(); ++q) {
+        int lo = sb[d - 1][q], hi = sb[d - 1][q + 1];
+        sb[d].push_back(lo);
+        sb[d].push_back(lo + (hi - lo) / 2);
+      }
+      sb[d].push_back(Ns);
+    }
+    bnd.resize(tau + 1);
+    for (int d = 0; d <= tau; ++d)
+      for (int v : sb[d]) bnd[d].push_back(nvar * v);
+    nleaves = 1 << tau;
+    this->leaf = 0;
+    for (int b = 0; b < nleaves; ++b) this->leaf = std::max(this->leaf, bnd[tau][b + 1] - bnd[tau][b]);
+    for (int d = 0; d <= tau; ++d) {
+      int m0 = bnd[d][1] - bnd[d][0];
+      for (size_t q = 0; q + 1 < bnd[d].size(); ++q)
+        if (bnd[d][q + 1] - bnd[d][q] != m0) throw Error(HODLR_ENOTIMPL, "uneven cluster trees are not built");
+    }
+    // spatial order
+    std::vector<int> sp(Ns);
+    if (dim == 1) {
+      for (int i = 0; i < Ns; ++i) sp[i] = i;
+    } else {
+      std::vector<std::pair<long long, int>> key(Ns);
+      int nbits = 1;
+      while ((1 << nbits) < G) ++nbits;
+      for (int p = 0; p < Ns; ++p) {
+        int ix = p % G, iy = p / G;
+        long long k = 0;
+        for (int b = 0; b < nbits; ++b) {
+          k |= (long long)((ix >> b) & 1) << (2 * b);
+          k |= (long long)((iy >> b) & 1) << (2 * b + 1);
+        }
+        key[p] = {k, p};
+      }
+      std::stable_sort(key.begin(), key.end(), [](auto& a, auto& b) { return a.first < b.first; });
+      for (int i = 0; i < Ns; ++i) sp[i] = key[i].second;
+    }
+    perm64.resize(N);
+    if (nvar == 1) {
+      for (int i = 0; i < N; ++i) perm64[i] = sp[i];
+    } else {
+      int pos = 0;
+      for (int b = 0; b < nleaves; ++b) {
+        int lo = sb[tau][b], hi = sb[tau][b + 1];
+        for (int i = lo; i < hi; ++i) perm64[pos++] = sp[i];
+        for (int i = lo; i < hi; ++i) perm64[pos++] = Ns + sp[i];
+      }
+    }
+    // physics geometry
+    ph.dim = dim; ph.G = G; ph.nvar = nvar; ph.nu = nu; ph.h = 1.0 / (G + 1);
+    int L = 1;
+    while (L < 2 * G - 1) L <<= 1;
+    ph.L = L; ph.L1 = 0; ph.L2 = 0;
+    if (dim == 1 && L > 4096) { ph.L2 = 2048; ph.L1 = L / 2048; }
+    if (dim == 2 && L > 4096) throw Error(HODLR_ENOTIMPL, "2-D grids above 2048 points per axis are not built");
+    w.assign(tau + 1, 0);
+    host_rank.assign(tau + 1, {});
+  }
+
+  int npairs(int l) const { return 1 << (l - 1); }
+  int msize(int d) const { return bnd[d][1] - bnd[d][0]; }  // node size at depth d
+
+  // ---------------------------------------------------------------- workspace plan / carve
+  void carve(Arena& ar) {
+    const size_t NN = (size_t)N;
+    qc = std::min(64, std::max(c, 2));
+    qc += qc & 1;
+    d_perm = ar.take<int>(N);
+    d_perm_plain = ar.take<int>(N);
+    d_mask.assign(tau + 1, nullptr);
+    for (int l = 1; l <= tau; ++l) d_mask[l] = ar.take<unsigned char>(N);
+    d_leafb = ar.take<int>(nleaves + 1);
+    F.assign(tau + 1, nullptr); U.assign(tau + 1, nullptr); CP.assign(tau + 1, nullptr);
+    dF[0].assign(tau + 1, nullptr); dF[1].assign(tau + 1, nullptr);
+    d_rank.assign(tau + 1, nullptr); d_piv.assign(tau + 1, nullptr); d_nodelog.assign(tau + 1, nullptr);
+    for (int l = 1; l <= tau; ++l) {
+      F[l] = ar.take<T>(NN * cap);
+      U[l] = ar.take<T>(NN * cap);
+      dF[0][l] = ar.take<T>(NN * cap);
+      dF[1][l] = ar.take<T>(NN * cap);
+      CP[l] = ar.take<T>((size_t)npairs(l) * 4 * cap * cap);
+      d_rank[l] = ar.take<int>(npairs(l));
+      d_piv[l] = ar.take<int>((size_t)npairs(l) * c);
+      d_nodelog[l] = ar.take<double>(npairs(l));
+    }
+    size_t nl2 = (size_t)nleaves * leaf * leaf;
+    A = ar.take<T>(nl2);
+    Ainv = ar.take<T>(nl2);
+    dA[0] = ar.take<T>(nl2);
+    dA[1] = ar.take<T>(nl2);
+    leaflog = ar.take<double>(nleaves);
+    // physics
+    size_t nemb = dim == 1 ? ph.L : (size_t)ph.L * ph.L;
+    lam0 = ar.take<T>(nemb);
+    lam1 = ar.take<T>(nemb);
+    tw = ar.take<T>(2 * (size_t)ph.L + 16);
+    coef = ar.take<double>(dim == 1 ? 2 * (size_t)G : 2 * (size_t)G * G);
+    if (dim == 2) Sdst = ar.take<T>((size_t)G * G);
+    fftw_bytes = std::max(fft_work_bytes(ph, qc, sizeof(T)), nemb * (sizeof(T) * 3) + 512);
+    fftw = ar.take<char>(fftw_bytes);
+    size_t nat = (size_t)nvar * Ns * qc;
+    nx = ar.take<T>(nat); na = ar.take<T>(nat); nb_ = ar.take<T>(nat); nu_ = ar.take<T>(nat);
+    nu2 = ar.take<T>(nat); ns = ar.take<T>(nat); ne = ar.take<T>(nat); nt = ar.take<T>(nat);
+    nw = ar.take<T>(nat);
+    // sketch
+    R = ar.take<T>(NN * c); KR = ar.take<T>(NN * c); KjR[0] = ar.take<T>(NN * c); KjR[1] = ar.take<T>(NN * c);
+    Y = ar.take<T>(NN * c);
+    S = ar.take<T>(NN * cap); KS = ar.take<T>(NN * cap); KjS[0] = ar.take<T>(NN * cap);
+    KjS[1] = ar.take<T>(NN * cap); dS = ar.take<T>(NN * cap); KdS = ar.take<T>(NN * cap);
+    YJ = ar.take<T>(NN * cap); Q1 = ar.take<T>(NN * cap);
+    int maxp = std::max(1, npairs(std::max(tau, 1)));
+    gram = ar.take<double>((size_t)maxp * c * c);
+    pwork = ar.take<double>((size_t)maxp * 2 * c * c);
+    RinvJ = ar.take<T>((size_t)maxp * cap * cap);
+    Rinv = ar.take<T>((size_t)maxp * cap * cap);
+    Linv_T = ar.take<T>((size_t)maxp * cap * cap);
+    sm1 = ar.take<T>((size_t)maxp * cap * cap);
+    sm2 = ar.take<T>((size_t)maxp * cap * cap);
+    sm3 = ar.take<T>((size_t)maxp * cap * cap);
+    int maxb = 2 * maxp;  // child blocks at the finest level
+    sw = ar.take<double>((size_t)maxb * cap * cap);
+    sx = ar.take<double>((size_t)maxp * cap * cap);
+    lw = ar.take<double>((size_t)maxp * cap * cap);
+    t1 = ar.take<double>((size_t)maxp * cap * cap);
+    t2 = ar.take<double>((size_t)maxp * cap * cap);
+    t3 = ar.take<double>((size_t)maxp * cap * cap);
+    phi = ar.take<double>((size_t)maxp * cap * cap);
+    // leaves / wide panels
+    for (int k = 0; k < 3; ++k) E[k] = ar.take<T>(NN * leaf);
+    wide = std::max(nwide * cap, 3 * leaf);
+    WP = ar.take<T>(NN * wide);
+    WZ = ar.take<T>(NN * wide);
+    LinvLeaf = ar.take<double>(nl2);
+    size_t qmax = (size_t)wide;
+    qmax = std::max<size_t>(qmax, (size_t)c);
+    fg = ar.take<T>((size_t)maxb * cap * qmax);
+    stb = ar.take<T>((size_t)maxb * cap * qmax);
+    tpan = ar.take<T>((size_t)maxb * 2 * cap * qmax);
+    nodeG = ar.take<T>((size_t)maxp * 4 * cap * cap * 12);
+    nodeX = ar.take<T>((size_t)maxp * 4 * cap * cap * 8);
+    vec_d = ar.take<double>(NN * 2);
+    vec_d2 = ar.take<double>(NN * 2);
+    vec_d3 = ar.take<double>(NN * 2);
+    vec_t = ar.take<T>(NN * 2);
+    red = ar.take<double>((size_t)std::max(maxb, nleaves) * 16 + 64);
+    res = ar.take<double>(256);
+    Afp = ar.take<double>(std::max(nl2, (size_t)maxb * cap * cap));
+    d_status = ar.take<int>(8);
+    size_t sbytes = std::max<size_t>(64u << 20, (size_t)4 * c * c * 8 * 640);
+    scratch.ptr = ar.take<char>(sbytes);
+    scratch.bytes = sbytes;
+  }
+
+  void upload_tree() {
+    std::vector<int> pp(N), pv(N);
+    for (int i = 0; i < N; ++i) {
+      int n = (int)perm64[i];
+      pp[i] = n;
+      pv[i] = nvar == 1 ? n : (n % Ns) + (n / Ns) * (Ns * qc);
+    }
+    HODLR_CUDA(cudaMemcpyAsync(d_perm, pv.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    HODLR_CUDA(cudaMemcpyAsync(d_perm_plain, pp.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    for (int l = 1; l <= tau; ++l) {
+      std::vector<unsigned char> m(N, 0);
+      const auto& b = bnd[l];
+      for (size_t q = 1; q + 1 < b.size(); q += 2)
+        for (int i = b[q]; i < b[q + 1]; ++i) m[i] = 1;
+      HODLR_CUDA(cudaMemcpyAsync(d_mask[l], m.data(), N, cudaMemcpyHostToDevice, st));
+      HODLR_CUDA(cudaStreamSynchronize(st));
+    }
+    HODLR_CUDA(cudaMemcpyAsync(d_leafb, bnd[tau].data(), (nleaves + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (dim == 2) dst_matrix<T>(G, Sdst, st);
+    if (ph.L1 == 0) twiddles<T>(ph.L, tw, st);
+    else {
+      twiddles<T>(ph.L1, tw, st);
+      twiddles<T>(ph.L2, tw + (ph.L1 / 2) * 2, st);
+    }
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+
+  void status_check(const char* what) {
+    int s = 0;
+    HODLR_CUDA(cudaMemcpyAsync(&s, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HODLR_CUDA(cudaStreamSynchronize(st));
+    if (s != 0) {
+      HODLR_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+      throw Error(s, std::string(what) + ": a Cholesky factorization failed (K~ not SPD)");
+    }
+  }
+
+  // ---------------------------------------------------------------- GEMM helpers
+  void gemmT(GemmArgs g) { gemm<T, T, T, T>(g, scratch, st); }
+  // per child block b at depth d: C_b (P x Q) = op(A[b])^T B[b]  (A, B row panels)
+  void block_tn(int d, int P, int Qn, const T* Ap, const T* Bp, long long ldb, T* C, long long ldc, long long sC,
+                double alpha = 1.0, double beta = 0.0) {
+    GemmArgs g;
+    int m = msize(d);
+    g.M = P; g.N = Qn; g.K = m;
+    g.A = Ap; g.lda = N; g.sA = m; g.tA = 1;
+    g.B = Bp; g.ldb = ldb; g.sB = m;
+    g.C = C; g.ldc = ldc; g.sC = sC;
+    g.alpha = alpha; g.beta = beta; g.batch = 1 << d;
+    gemmT(g);
+  }
+
+  // out -= sum over levels in [l0, l1] of H_l X (or dH^(j)_l X) ; X, out: N x q row panels
+  void offdiag(int l0, int l1, int j, const T* X, long long ldx, int q, T* out, long long ldo, double sign = -1.0) {
+    for (int l = l0; l <= l1; ++l) {
+      int wl = w[l];
+      if (wl == 0 || q == 0) continue;
+      int m = msize(l);
+      int nbk = 1 << l;
+      const T* Fl = F[l];
+      // T1_b = F[b]^T X[b]   (wl x q per child block, ld wl)
+      block_tn(l, wl, q, Fl, X, ldx, tpan, wl, (long long)wl * q);
+      GemmArgs g;
+      g.M = m; g.N = q; g.K = wl;
+      g.lda = N; g.sA = m;
+      g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
+      g.C = out; g.ldc = ldo; g.sC = m;
+      g.alpha = sign; g.beta = 1.0; g.batch = nbk;
+      if (j < 0) {
+        g.A = Fl; g.B = tpan;
+        gemmT(g);
+      } else {
+        const T* dFl = dF[j][l];
+        T* t2p = tpan + (size_t)nbk * wl * q;
+        block_tn(l, wl, q, dFl, X, ldx, t2p, wl, (long long)wl * q);
+        g.A = dFl; g.B = tpan;          // dQ (B~^T x2) and dB~ (Q^T x1)
+        gemmT(g);
+        g.A = Fl; g.B = t2p;            // Q (dB~^T x2) and B~ (dQ^T x1)
+        gemmT(g);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- physics product
+  const double* th = theta_built;
+  void set_physics(const double* theta) {
+    matern_spectra<T>(ph, theta[0], theta[1], lam0, lam1, fftw, tw, st);
+    tridiag_tables(ph, theta[2], coef, st);
+  }
+  void Ainv_nat(const T* in, T* out, int q) {
+    solve_A<T>(ph, q, in, Ns, out, Ns, coef, Sdst, nw, scratch, st);
+  }
+  // K X, K_ell X, K_kappa X on a tree-order panel (q columns); any output may be null
+  void apply(const T* X, long long ldx, int q, T* oK, T* oL, T* oKap, long long ldo) {
+    const double s2 = th[0], kap = th[2], t2 = th[3];
+    (void)s2;
+    const size_t vs = (size_t)Ns * qc;   // variable stride in natural buffers
+    for (int c0 = 0; c0 < q; c0 += qc) {
+      int qq = std::min(qc, q - c0);
+      const T* Xc = X + (size_t)c0 * ldx;
+      permute_rows<T, T>(Xc, ldx, nx, Ns, d_perm, N, qq, 1, st);
+      auto out = [&](T* dst, const T* src) {
+        if (dst) permute_rows<T, T>(src, Ns, dst + (size_t)c0 * ldo, ldo, d_perm, N, qq, 0, st);
+      };
+      if (nvar == 1) {
+        Ainv_nat(nx, na, qq);                                              // a = A^{-1} x
+        if (oKap) Ainv_nat(na, nb_, qq);                                   // b = A^{-2} x
+        if (oK || oKap || oL) fft_convolve<T>(ph, qq, na, Ns, lam0, oL ? lam1 : nullptr, nu_, nu2, Ns, fftw, tw, st);
+        if (oKap) fft_convolve<T>(ph, qq, nb_, Ns, lam0, nullptr, ns, nullptr, Ns, fftw, tw, st);
+        if (oK || oKap) Ainv_nat(nu_, ne, qq);                             // e = A^{-1} K_u a
+        if (oK) {
+          out(oK, ne);
+          axpby<T>(N, qq, t2, Xc, ldx, 1.0, oK + (size_t)c0 * ldo, ldo, st);
+        }
+        if (oL) {
+          Ainv_nat(nu2, nt, qq);
+          out(oL, nt);
+        }
+        if (oKap) {
+          axpby<T>(Ns, qq, 1.0, ns, Ns, 1.0, ne, Ns, st);                  // e + K_u b
+          Ainv_nat(ne, nt, qq);
+          axpby<T>(Ns, qq, 0.0, nt, Ns, -2.0 * kap, nt, Ns, st);
+          out(oKap, nt);
+        }
+        napply += (long long)qq * ((oK ? 1 : 0) + (oL ? 1 : 0) + (oKap ? 1 : 0));
+      } else {
+        T* x1 = nx;
+        T* x2 = nx + vs;
+        T* a = na;
+        T* wv = na + vs;
+        Ainv_nat(x2, a, qq);                                               // a = A^{-1} x2
+        axpby<T>(Ns, qq, 1.0, x1, Ns, 0.0, wv, Ns, st);
+        axpby<T>(Ns, qq, 1.0, a, Ns, 1.0, wv, Ns, st);                     // w = x1 + a  (L^T x)
+        T* u = nu_;        // [u; c1]
+        T* u2 = nu2;       // [u'; c2]
+        T* s = ns;         // [s; c3]
+        if (oK || oKap || oL) fft_convolve<T>(ph, qq, wv, Ns, lam0, oL ? lam1 : nullptr, u, u2, Ns, fftw, tw, st);
+        if (oK || oKap) Ainv_nat(u, u + vs, qq);                           // c1 = A^{-1} u
+        if (oK) {
+          out(oK, u);
+          axpby<T>(N, qq, t2, Xc, ldx, 1.0, oK + (size_t)c0 * ldo, ldo, st);
+        }
+        if (oL) {
+          Ainv_nat(u2, u2 + vs, qq);
+          out(oL, u2);
+        }
+        if (oKap) {
+          T* b = nb_;
+          Ainv_nat(a, b, qq);                                              // b = A^{-2} x2
+          fft_convolve<T>(ph, qq, b, Ns, lam0, nullptr, s, nullptr, Ns, fftw, tw, st);   // s = K_u b
+          axpby<T>(Ns, qq, 1.0, u + vs, Ns, 0.0, nt, Ns, st);
+          axpby<T>(Ns, qq, 1.0, s, Ns, 1.0, nt, Ns, st);                   // c1 + s
+          Ainv_nat(nt, s + vs, qq);                                        // c3
+          axpby<T>(Ns, qq, 0.0, s, Ns, -2.0 * kap, s, Ns, st);             // -2 kappa [s; c3]
+          axpby<T>(Ns, qq, 0.0, s + vs, Ns, -2.0 * kap, s + vs, Ns, st);
+          out(oKap, s);
+        }
+        napply += (long long)qq * ((oK ? 1 : 0) + (oL ? 1 : 0) + (oKap ? 1 : 0));
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- build (Alg. 1, Sec. 3.2.2, Alg. 2, Sec. 3.3)
+  void build(const double* theta) override {
+    for (int k = 0; k < 4; ++k) {
+      if (!(theta[k] > 0.0) || !std::isfinite(theta[k])) throw Error(HODLR_EINVAL, "theta must be positive and finite");
+      theta_built[k] = theta[k];
+    }
+    built = false;
+    napply = 0;
+    HODLR_CUDA(cudaMemsetAsync(d_status, 0, 8 * sizeof(int), st));
+    set_physics(theta);
+    const double thr = std::max(tol, guard);
+    for (int l = 1; l <= tau; ++l) {
+      const int np = npairs(l);
+      const int m = msize(l);          // child block size
+      // --- sketch of the level's blocks: Y = (K - sum_{l'<l} H^(l')) R^(l)
+      probe_panel<T>(N, c, l, 0, seed, d_mask[l], R, N, st);
+      apply(R, N, c, KR, KjR[0], KjR[1], N);
+      HODLR_CUDA(cudaMemcpyAsync(Y, KR, sizeof(T) * (size_t)N * c, cudaMemcpyDeviceToDevice, st));
+      offdiag(1, l - 1, -1, R, N, c, Y, N);
+      // --- pivoted QR of each left-child block of Y via its FP64 Gram (Alg. 1 step 3)
+      {
+        GemmArgs g;
+        g.M = c; g.N = c; g.K = m;
+        g.A = Y; g.lda = N; g.sA = 2 * m; g.tA = 1;
+        g.B = Y; g.ldb = N; g.sB = 2 * m;
+        g.C = gram; g.ldc = c; g.sC = (long long)c * c; g.batch = np;
+        gemm<T, T, double, double>(g, scratch, st);
+      }
+      pivoted_cholesky<T>(np, c, cap, cap, gram, thr, d_rank[l], d_piv[l], RinvJ, frozen ? 1 : 0, pwork, d_status, st);
+      status_check("frozen pivots");
+      host_rank[l].resize(np);
+      HODLR_CUDA(cudaMemcpyAsync(host_rank[l].data(), d_rank[l], np * sizeof(int), cudaMemcpyDeviceToHost, st));
+      HODLR_CUDA(cudaStreamSynchronize(st));
+      int wl = 0;
+      for (int r : host_rank[l]) wl = std::max(wl, r);
+      w[l] = wl;
+      fill<T>(F[l], T(0), (long long)N * cap, st);
+      fill<T>(dF[0][l], T(0), (long long)N * cap, st);
+      fill<T>(dF[1][l], T(0), (long long)N * cap, st);
+      if (wl == 0) continue;
+      // --- Q = Y_J R_J^{-1}, re-orthogonalised once (CholQR on the FP64 Gram)
+      gather_columns<T>(np, m, 2LL * m, Y, N, d_piv[l], c, d_rank[l], wl, YJ, N, st);
+      pair_nn(l, wl, YJ, RinvJ, cap, Q1, 1.0, 0.0);
+      {
+        GemmArgs g;
+        g.M = wl; g.N = wl; g.K = m;
+        g.A = Q1; g.lda = N; g.sA = 2 * m; g.tA = 1;
+        g.B = Q1; g.ldb = N; g.sB = 2 * m;
+        g.C = gram; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = np;
+        gemm<T, T, double, double>(g, scratch, st);
+      }
+      potrf_lower(np, wl, gram, wl, (long long)wl * wl, d_rank[l], nullptr, d_status, st);
+      trtri_lower(np, wl, gram, wl, (long long)wl * wl, t1, st);
+      convert<double, T>(t1, Linv_T, (long long)np * wl * wl, st);
+      status_check("CholQR");
+      // Q = Q1 Linv^T into the left-child rows of F[l]
+      {
+        GemmArgs g;
+        g.M = m; g.N = wl; g.K = wl;
+        g.A = Q1; g.lda = N; g.sA = 2 * m;
+        g.B = Linv_T; g.ldb = wl; g.sB = (long long)wl * wl; g.tB = 1;
+        g.C = F[l]; g.ldc = N; g.sC = 2 * m; g.batch = np;
+        gemmT(g);
+      }
+      // R^{-1} of Y_J = Q R:  RinvJ * Linv^T   (wl x wl per pair)
+      {
+        GemmArgs g;
+        g.M = wl; g.N = wl; g.K = wl;
+        g.A = RinvJ; g.lda = cap; g.sA = (long long)cap * cap;
+        g.B = Linv_T; g.ldb = wl; g.sB = (long long)wl * wl; g.tB = 1;
+        g.C = Rinv; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = np;
+        gemmT(g);
+      }
+      // --- projection: Z = (K - sum H) S^(l), S = [Q; 0];  B~ = Z[c2]
+      HODLR_CUDA(cudaMemcpyAsync(S, F[l], sizeof(T) * (size_t)N * wl, cudaMemcpyDeviceToDevice, st));
+      apply(S, N, wl, KS, KjS[0], KjS[1], N);
+      offdiag(1, l - 1, -1, S, N, wl, KS, N);
+      copy_rows_c2(l, wl, KS, F[l]);
+      // --- derivatives (Sec. 3.3) for ell (j=0) and kappa (j=1)
+      for (int j = 0; j < 2; ++j) {
+        T* dY = KjR[j];
+        offdiag(1, l - 1, j, R, N, c, dY, N);                              // dY = K_j R - sum dH R
+        gather_columns<T>(np, m, 2LL * m, dY, N, d_piv[l], c, d_rank[l], wl, YJ, N, st);
+        // Alg. 2 step 1: Y' = Q^T dY R^{-1}
+        {
+          GemmArgs g;
+          g.M = wl; g.N = wl; g.K = m;
+          g.A = F[l]; g.lda = N; g.sA = 2 * m; g.tA = 1;
+          g.B = YJ; g.ldb = N; g.sB = 2 * m;
+          g.C = sm1; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = np;
+          gemmT(g);
+        }
+        small_nn(np, wl, sm1, Rinv, sm2);                                  // Y' = (Q^T dY) R^{-1}
+        alg2_core<T>(np, wl, sm2, sm3, st);                                    // step 2: M2 = dOmega - Y'
+        // step 3: dQ = dY R^{-1} + Q M2 = Q dOmega + (I - Q Q^T) dY R^{-1}
+        pair_nn(l, wl, YJ, Rinv, wl, dF[j][l], 1.0, 0.0);
+        pair_nn(l, wl, F[l], sm3, wl, dF[j][l], 1.0, 1.0);
+        // dZ = (K_j - sum dH) S + (K - sum H) dS,  dS = [dQ; 0]
+        HODLR_CUDA(cudaMemcpyAsync(dS, dF[j][l], sizeof(T) * (size_t)N * wl, cudaMemcpyDeviceToDevice, st));
+        apply(dS, N, wl, KdS, nullptr, nullptr, N);
+        offdiag(1, l - 1, -1, dS, N, wl, KdS, N);
+        T* dZ = KjS[j];
+        offdiag(1, l - 1, j, S, N, wl, dZ, N);
+        axpby<T>(N, wl, 1.0, KdS, N, 1.0, dZ, N, st);
+        copy_rows_c2(l, wl, dZ, dF[j][l]);
+      }
+    }
+    build_leaves();
+    factor();
+    for (int k = 0; k < 4; ++k) theta_built[k] = theta[k];
+    built = true;
+  }
+
+  // C[c1 rows of pair p] = alpha * A[c1 rows of p] * B_p + beta * C   (m x wl, B_p: wl x wl, ld ldb)
+  void pair_nn(int l, int wl, const T* Ap, const T* Bp, int ldb, T* Cp, double alpha, double beta) {
+    int m = msize(l);
+    GemmArgs g;
+    g.M = m; g.N = wl; g.K = wl;
+    g.A = Ap; g.lda = N; g.sA = 2 * m;
+    g.B = Bp; g.ldb = ldb; g.sB = (long long)ldb * ldb;
+    g.C = Cp; g.ldc = N; g.sC = 2 * m;
+    g.alpha = alpha; g.beta = beta; g.batch = npairs(l);
+    if (ldb != wl) g.sB = (long long)ldb * ldb;
+    gemmT(g);
+  }
+  void small_nn(int nb, int n, const T* Ap, const T* Bp, T* Cp) {
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = n;
+    g.A = Ap; g.lda = n; g.sA = (long long)n * n;
+    g.B = Bp; g.ldb = n; g.sB = (long long)n * n;
+    g.C = Cp; g.ldc = n; g.sC = (long long)n * n; g.batch = nb;
+    gemmT(g);
+  }
+  // copy the right-child rows of src (N x wl) into dst
+  void copy_rows_c2(int l, int wl, const T* src, T* dst) {
+    int m = msize(l);
+    copy_blocks<T, T>(npairs(l), m, wl, src + m, N, 2LL * m, dst + m, N, 2LL * m, 1.0, st);
+  }
+
+  // ---------------------------------------------------------------- leaves (eq. leaf sample, eq. diag diff)
+  void build_leaves() {
+    const int nl = leaf;
+    // S_leaf = stacked identities
+    T* Sl = WP;  // N x nl
+    fill<T>(Sl, T(0), (long long)N * nl, st);
+    identity_blocks(Sl);
+    apply(Sl, N, nl, E[0], E[1], E[2], N);
+    offdiag(1, tau, -1, Sl, N, nl, E[0], N);
+    offdiag(1, tau, 0, Sl, N, nl, E[1], N);
+    offdiag(1, tau, 1, Sl, N, nl, E[2], N);
+    extract_leaves<T, double>(nleaves, nl, d_leafb, E[0], N, Afp, st);
+    convert<double, T>(Afp, A, (long long)nleaves * nl * nl, st);
+    extract_leaves<T, T>(nleaves, nl, d_leafb, E[1], N, dA[0], st);
+    extract_leaves<T, T>(nleaves, nl, d_leafb, E[2], N, dA[1], st);
+    // FP64 leaf Cholesky, log-det and inverse
+    potrf_lower(nleaves, nl, Afp, nl, (long long)nl * nl, nullptr, leaflog, d_status, st);
+    double* Linv = LinvLeaf;
+    trtri_lower(nleaves, nl, Afp, nl, (long long)nl * nl, Linv, st);
+    {
+      GemmArgs g;  // A^{-1} = L^{-T} L^{-1}
+      g.M = nl; g.N = nl; g.K = nl;
+      g.A = Linv; g.lda = nl; g.sA = (long long)nl * nl; g.tA = 1;
+      g.B = Linv; g.ldb = nl; g.sB = (long long)nl * nl;
+      g.C = Ainv; g.ldc = nl; g.sC = (long long)nl * nl; g.batch = nleaves;
+      gemm<double, double, T, double>(g, scratch, st);
+    }
+    status_check("leaf Cholesky");
+  }
+  void identity_blocks(T* Sl);
+
+  // ---------------------------------------------------------------- factorization (App. C)
+  // solve with the block-diagonal of the depth-d subtrees:  out = diag_v(K~_v^{-1}) in
+  void solve_depth(const T* in, long long ldi, T* out, long long ldo, int q, int d) {
+    const int nl = leaf;
+    {
+      GemmArgs g;
+      g.M = nl; g.N = q; g.K = nl;
+      g.A = Ainv; g.lda = nl; g.sA = (long long)nl * nl;
+      g.B = in; g.ldb = ldi; g.sB = nl;
+      g.C = out; g.ldc = ldo; g.sC = nl; g.batch = nleaves;
+      gemmT(g);
+    }
+    for (int l = tau; l > d; --l) {
+      int wl = w[l];
+      if (wl == 0) continue;
+      int m = msize(l), np = npairs(l), nbk = 1 << l;
+      // FG^T_b = out[b]^T F[b]   (q x wl per child block, consecutive -> per pair q x 2wl = [g f]^T)
+      GemmArgs g;
+      g.M = q; g.N = wl; g.K = m;
+      g.A = out; g.lda = ldo; g.sA = m; g.tA = 1;
+      g.B = F[l]; g.ldb = N; g.sB = m;
+      g.C = fg; g.ldc = q; g.sC = (long long)q * wl; g.batch = nbk;
+      gemmT(g);
+      // ST^T_p = FG^T_p (CP_p)^T, CP = C^{-1} P  ->  ST = C^{-1} [f; g] = [s; t]
+      GemmArgs h;
+      h.M = q; h.N = 2 * wl; h.K = 2 * wl;
+      h.A = fg; h.lda = q; h.sA = 2LL * q * wl;
+      h.B = CP[l]; h.ldb = 2 * wl; h.sB = 4LL * wl * wl; h.tB = 1;
+      h.C = stb; h.ldc = q; h.sC = 2LL * q * wl; h.batch = np;
+      gemmT(h);
+      // out[b] -= U[b] (ST^T_b)^T ; ST^T_b is the b-th q x wl block (s for c1, t for c2)
+      GemmArgs k;
+      k.M = m; k.N = q; k.K = wl;
+      k.A = U[l]; k.lda = N; k.sA = m;
+      k.B = stb; k.ldb = q; k.sB = (long long)q * wl; k.tB = 1;
+      k.C = out; k.ldc = ldo; k.sC = m;
+      k.alpha = -1.0; k.beta = 1.0; k.batch = nbk;
+      gemmT(k);
+    }
+  }
+
+  void factor() {
+    double* sg = Afp;  // Grams of the child blocks (FP64): even -> Sw, odd -> Sx
+    for (int l = tau; l >= 1; --l) {
+      int wl = w[l];
+      int np = npairs(l);
+      if (wl == 0) {
+        fill<double>(d_nodelog[l], 0.0, np, st);
+        continue;
+      }
+      solve_depth(F[l], N, U[l], N, wl, l);
+      {
+        GemmArgs g;
+        int m = msize(l);
+        g.M = wl; g.N = wl; g.K = m;
+        g.A = F[l]; g.lda = N; g.sA = m; g.tA = 1;
+        g.B = U[l]; g.ldb = N; g.sB = m;
+        g.C = sg; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = 1 << l;
+        gemm<T, T, double, double>(g, scratch, st);
+      }
+      const long long w2 = (long long)wl * wl;
+      // split into Sw (even blocks) and Sx (odd blocks)
+      copy_blocks<double, double>(np, wl, wl, sg, wl, 2 * w2, sw, wl, w2, 1.0, st);
+      copy_blocks<double, double>(np, wl, wl, sg + w2, wl, 2 * w2, sx, wl, w2, 1.0, st);
+      HODLR_CUDA(cudaMemcpyAsync(lw, sw, sizeof(double) * np * w2, cudaMemcpyDeviceToDevice, st));
+      potrf_lower(np, wl, lw, wl, w2, d_rank[l], nullptr, d_status, st);     // Sw (+I padded) = Lw Lw^T
+      // use the padded Sw consistently: Sw <- Lw Lw^T
+      dgemm_small(np, wl, lw, 0, lw, 1, sw, 1.0, 0.0);
+      dgemm_small(np, wl, sx, 0, lw, 0, t1, 1.0, 0.0);                        // Sx Lw
+      dgemm_small(np, wl, lw, 1, t1, 0, t2, -1.0, 0.0);                       // -Lw^T Sx Lw
+      shift_identity(np, wl, t2, wl, w2, 1.0, 1.0, st);                       // E = I - Lw^T Sx Lw
+      potrf_lower(np, wl, t2, wl, w2, nullptr, d_nodelog[l], d_status, st);  // E = LE LE^T
+      trtri_lower(np, wl, t2, wl, w2, t3, st);                                // LE^{-1}
+      dgemm_small(np, wl, lw, 0, t3, 1, t1, 1.0, 0.0);                        // V = Lw LE^{-T}
+      dgemm_small(np, wl, t1, 0, t1, 1, t2, 1.0, 0.0);                        // Lw E^{-1} Lw^T
+      dgemm_small(np, wl, sx, 0, t2, 0, phi, 1.0, 0.0);                       // Sx Lw E^{-1} Lw^T
+      shift_identity(np, wl, phi, wl, w2, 1.0, 1.0, st);                      // Phi = (I - Sx Sw)^{-1}
+      dgemm_small(np, wl, phi, 0, sx, 0, t1, 1.0, 0.0);                       // Phi Sx
+      dgemm_small(np, wl, sw, 0, phi, 0, t2, 1.0, 0.0);                       // Sw Phi
+      dgemm_small(np, wl, sw, 0, t1, 0, t3, 1.0, 0.0);                        // Sw Phi Sx
+      shift_identity(np, wl, t3, wl, w2, 1.0, 1.0, st);                       // I + Sw Phi Sx
+      // CP = C^{-1} P = [[-Phi Sx, Phi], [I + Sw Phi Sx, -Sw Phi]]  (2wl x 2wl)
+      const long long s4 = 4 * w2, ld2 = 2 * wl;
+      T* cp = CP[l];
+      copy_blocks<double, T>(np, wl, wl, t1, wl, w2, cp, ld2, s4, -1.0, st);
+      copy_blocks<double, T>(np, wl, wl, phi, wl, w2, cp + wl * ld2, ld2, s4, 1.0, st);
+      copy_blocks<double, T>(np, wl, wl, t3, wl, w2, cp + wl, ld2, s4, 1.0, st);
+      copy_blocks<double, T>(np, wl, wl, t2, wl, w2, cp + wl + wl * ld2, ld2, s4, -1.0, st);
+      status_check("SMW core");
+    }
+    // total log-det: leaves + nodes (Sylvester)
+    sum_doubles(leaflog, nleaves, res + 0, 0, st);
+    for (int l = 1; l <= tau; ++l) sum_doubles(d_nodelog[l], npairs(l), res + 0, 1, st);
+    HODLR_CUDA(cudaMemcpyAsync(&logdet, res, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HODLR_CUDA(cudaStreamSynchronize(st));
+    if (!std::isfinite(logdet)) throw Error(HODLR_ENUMERIC, "log-determinant is not finite");
+  }
+  void dgemm_small(int nb, int n, const double* a, int ta, const double* b, int tb, double* cc, double alpha,
+                   double beta) {
+    GemmArgs g;
+    g.M = n; g.N = n; g.K = n;
+    g.A = a; g.lda = n; g.sA = (long long)n * n; g.tA = ta;
+    g.B = b; g.ldb = n; g.sB = (long long)n * n; g.tB = tb;
+    g.C = cc; g.ldc = n; g.sC = (long long)n * n;
+    g.alpha = alpha; g.beta = beta; g.batch = nb;
+    gemm<double, double, double, double>(g, scratch, st);
+  }
+
+  // ---------------------------------------------------------------- HODLR products (mixed vector type V)
+  // out = M X for M = K~ (j<0) or K~_j, at depth d: leaves + off-diagonal levels > d
+  template <class V>
+  void matvec(int j, const V* X, long long ldx, V* out, long long ldo, int q, int d) {
+    const int nl = leaf;
+    const T* Lf = j < 0 ? A : dA[j];
+    {
+      GemmArgs g;
+      g.M = nl; g.N = q; g.K = nl;
+      g.A = Lf; g.lda = nl; g.sA = (long long)nl * nl;
+      g.B = X; g.ldb = ldx; g.sB = nl;
+      g.C = out; g.ldc = ldo; g.sC = nl; g.batch = nleaves;
+      gemm<T, V, V, double>(g, scratch, st);
+    }
+    for (int l = d + 1; l <= tau; ++l) {
+      int wl = w[l];
+      if (wl == 0) continue;
+      int m = msize(l), nbk = 1 << l;
+      V* tp = (V*)tpan;
+      auto tn = [&](const T* Fp, V* C) {
+        GemmArgs g;
+        g.M = wl; g.N = q; g.K = m;
+        g.A = Fp; g.lda = N; g.sA = m; g.tA = 1;
+        g.B = X; g.ldb = ldx; g.sB = m;
+        g.C = C; g.ldc = wl; g.sC = (long long)wl * q; g.batch = nbk;
+        gemm<T, V, V, double>(g, scratch, st);
+      };
+      auto nn = [&](const T* Fp, const V* Bp) {
+        GemmArgs g;
+        g.M = m; g.N = q; g.K = wl;
+        g.A = Fp; g.lda = N; g.sA = m;
+        g.B = Bp; g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
+        g.C = out; g.ldc = ldo; g.sC = m;
+        g.beta = 1.0; g.batch = nbk;
+        gemm<T, V, V, double>(g, scratch, st);
+      };
+      if (j < 0) {
+        tn(F[l], tp);
+        nn(F[l], tp);
+      } else {
+        V* tp2 = tp + (size_t)nbk * wl * q;
+        tn(F[l], tp);
+        tn(dF[j][l], tp2);
+        nn(dF[j][l], tp);
+        nn(F[l], tp2);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- solve with refinement
+  // alpha = K~^{-1} b for a tree-order FP64 vector (FP64 path: direct; mixed: FP32 solve + FP64
+  // iterative refinement against the stored K~).
+  void solve_tree(const double* b, double* x) {
+    if (sizeof(T) == 8) {
+      solve_depth((const T*)b, N, (T*)x, N, 1, 0);
+      return;
+    }
+    // x0 = solve(b)
+    convert<double, T>(b, vec_t, N, st);
+    solve_depth(vec_t, N, (T*)vec_d3, N, 1, 0);
+    convert<T, double>((T*)vec_d3, x, N, st);
+    for (int it = 0; it < 3; ++it) {
+      matvec<double>(-1, x, N, vec_d2, N, 1, 0);                 // K~ x (FP64 vectors)
+      axpby<double>(N, 1, 1.0, b, N, -1.0, vec_d2, N, st);       // r = b - K~ x
+      convert<double, T>(vec_d2, vec_t, N, st);
+      solve_depth(vec_t, N, (T*)vec_d3, N, 1, 0);
+      convert<T, double>((T*)vec_d3, vec_d2, N, st);
+      axpby<double>(N, 1, 1.0, vec_d2, N, 1.0, x, N, st);
+    }
+  }
+
+  // ---------------------------------------------------------------- exact traces (App. B)
+  // t[i] = tr(K~^{-1} M_i), f[i][j] = tr(K~^{-1} M_i K~^{-1} M_j), M = (I, K~_ell, K~_kappa)
+  void traces_impl(bool fisher, double* t_out, double* f_out) {
+    const int nl = leaf;
+    double* acc = res + 16;   // 3 + 9 accumulators
+    HODLR_CUDA(cudaMemsetAsync(acc, 0, 12 * sizeof(double), st));
+    // leaves: Lambda_0 = A^{-1}, Lambda_i = A^{-1} dA_i
+    T* Lam = WZ;
+    const long long nl2 = (long long)nl * nl;
+    HODLR_CUDA(cudaMemcpyAsync(Lam, Ainv, sizeof(T) * nleaves * nl2, cudaMemcpyDeviceToDevice, st));
+    for (int i = 0; i < 2; ++i) {
+      GemmArgs g;
+      g.M = nl; g.N = nl; g.K = nl;
+      g.A = Ainv; g.lda = nl; g.sA = nl2;
+      g.B = dA[i]; g.ldb = nl; g.sB = nl2;
+      g.C = Lam + (size_t)(i + 1) * nleaves * nl2; g.ldc = nl; g.sC = nl2; g.batch = nleaves;
+      gemmT(g);
+    }
+    for (int i = 0; i < 3; ++i) {
+      const T* Li = Lam + (size_t)i * nleaves * nl2;
+      trace_products<T>(nleaves, nl, nullptr, Li, nl, nl2, nullptr, 0, 0, 0, red, st);
+      sum_doubles(red, nleaves, acc + i, 1, st);
+      if (!fisher) continue;
+      for (int j = i; j < 3; ++j) {
+        const T* Lj = Lam + (size_t)j * nleaves * nl2;
+        trace_products<T>(nleaves, nl, nullptr, Li, nl, nl2, Lj, nl, nl2, 0, red, st);
+        sum_doubles(red, nleaves, acc + 3 + 3 * i + j, 1, st);
+      }
+    }
+    // nodes, level by level
+    for (int l = 1; l <= tau; ++l) {
+      int wl = w[l];
+      if (wl == 0) continue;
+      const int np = npairs(l), m = msize(l), w2 = 2 * wl;
+      const long long pw = (long long)N * w2;   // one 2wl-wide panel
+      // WP = [P | Y1 | Y2 | Pi1 | Pi2]; P = U_v as a panel: c1 rows [W~, 0], c2 rows [0, X~]
+      T* P = WP;
+      fill<T>(P, T(0), pw, st);
+      copy_blocks<T, T>(np, m, wl, U[l], N, 2LL * m, P, N, 2LL * m, 1.0, st);
+      copy_blocks<T, T>(np, m, wl, U[l] + m, N, 2LL * m, P + m + (size_t)wl * N, N, 2LL * m, 1.0, st);
+      for (int i = 0; i < 2; ++i) matvec<T>(i, P, N, P + (size_t)(i + 1) * pw, N, w2, l - 1);
+      int nsolve = 3;
+      if (fisher) {
+        for (int i = 0; i < 2; ++i) {
+          // Pi_i: c1 rows [dQ | Q], c2 rows [B~ | dB~]
+          T* Pi = P + (size_t)(3 + i) * pw;
+          copy_blocks<T, T>(np, m, wl, dF[i][l], N, 2LL * m, Pi, N, 2LL * m, 1.0, st);
+          copy_blocks<T, T>(np, m, wl, F[l], N, 2LL * m, Pi + (size_t)wl * N, N, 2LL * m, 1.0, st);
+          copy_blocks<T, T>(np, m, wl, F[l] + m, N, 2LL * m, Pi + m, N, 2LL * m, 1.0, st);
+          copy_blocks<T, T>(np, m, wl, dF[i][l] + m, N, 2LL * m, Pi + m + (size_t)wl * N, N, 2LL * m, 1.0, st);
+        }
+        nsolve = 5;
+        solve_depth(P, N, WZ, N, nsolve * w2, l);
+      }
+      // per-node Grams (2wl x 2wl): G_i = P^T Y_i
+      const long long g2 = (long long)w2 * w2;
+      T* Gm = nodeG;               // 3 blocks of np * g2
+      T* Tm = nodeG + 3 * np * g2; // 6 blocks
+      T* Xm = nodeX;               // CP G_i
+      for (int i = 0; i < 3; ++i) node_tn(l, w2, P, P + (size_t)i * pw, Gm + (size_t)i * np * g2);
+      for (int i = 0; i < 3; ++i) dgemm_nodes(np, w2, CP[l], Gm + (size_t)i * np * g2, Xm + (size_t)i * np * g2);
+      for (int i = 0; i < 3; ++i) {
+        trace_products<T>(np, w2, nullptr, Xm + (size_t)i * np * g2, w2, g2, nullptr, 0, 0, 0, red, st);
+        sum_doubles_scaled(red, np, acc + i, -1.0);
+      }
+      if (!fisher) continue;
+      int tix = 0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j, ++tix) {
+          T* Tij = Tm + (size_t)tix * np * g2;
+          node_tn(l, w2, P + (size_t)i * pw, WZ + (size_t)j * pw, Tij);       // T_ij = Y_i^T Z_j
+          // - tr(CP T_ij) - tr(CP T_ij^T)
+          trace_products<T>(np, w2, nullptr, CP[l], w2, g2, Tij, w2, g2, 0, red, st);
+          sum_doubles_scaled(red, np, acc + 3 + 3 * i + j, -1.0);
+          trace_products<T>(np, w2, nullptr, CP[l], w2, g2, Tij, w2, g2, 1, red, st);
+          sum_doubles_scaled(red, np, acc + 3 + 3 * i + j, -1.0);
+          // + tr((CP G_i)(CP G_j))
+          trace_products<T>(np, w2, nullptr, Xm + (size_t)i * np * g2, w2, g2, Xm + (size_t)j * np * g2, w2, g2, 0,
+                            red, st);
+          sum_doubles_scaled(red, np, acc + 3 + 3 * i + j, 1.0);
+          // cross term of the two off-diagonal blocks: 2 tr((A_j^T K1^{-1} A_i)(B_i^T K2^{-1} B_j))
+          if (i >= 1 && j >= 1) {
+            T* Pi_i = P + (size_t)(2 + i) * pw;
+            T* Pi_j = P + (size_t)(2 + j) * pw;
+            T* Pb_i = WZ + (size_t)(2 + i) * pw;
+            T* Pb_j = WZ + (size_t)(2 + j) * pw;
+            T* Gji = nodeX + 3 * np * g2;       // per child block (2^l blocks)
+            T* Gij = Gji + (size_t)2 * np * g2;
+            child_tn(l, w2, Pi_j, Pb_i, Gji);   // Gamma_ji[b] = Pi_j[b]^T Pibar_i[b]
+            child_tn(l, w2, Pi_i, Pb_j, Gij);   // Gamma_ij[b]
+            // tr(Gamma_ji[c1] Gamma_ij[c2]): even blocks of Gji with odd blocks of Gij
+            trace_products<T>(np, w2, nullptr, Gji, w2, 2 * g2, Gij + g2, w2, 2 * g2, 0, red, st);
+            sum_doubles_scaled(red, np, acc + 3 + 3 * i + j, 2.0);
+          }
+        }
+    }
+    double h[12];
+    HODLR_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    HODLR_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < 3; ++i) t_out[i] = h[i];
+    if (fisher)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) f_out[3 * i + j] = i <= j ? h[3 + 3 * i + j] : h[3 + 3 * j + i];
+  }
+  // per-node (rows of both children) Gram C_v = A_v^T B_v, 2w x 2w
+  void node_tn(int l, int w2, const T* Ap, const T* Bp, T* Cp) {
+    int mm = 2 * msize(l);
+    GemmArgs g;
+    g.M = w2; g.N = w2; g.K = mm;
+    g.A = Ap; g.lda = N; g.sA = mm; g.tA = 1;
+    g.B = Bp; g.ldb = N; g.sB = mm;
+    g.C = Cp; g.ldc = w2; g.sC = (long long)w2 * w2; g.batch = npairs(l);
+    gemmT(g);
+  }
+  void child_tn(int l, int w2, const T* Ap, const T* Bp, T* Cp) {
+    int mm = msize(l);
+    GemmArgs g;
+    g.M = w2; g.N = w2; g.K = mm;
+    g.A = Ap; g.lda = N; g.sA = mm; g.tA = 1;
+    g.B = Bp; g.ldb = N; g.sB = mm;
+    g.C = Cp; g.ldc = w2; g.sC = (long long)w2 * w2; g.batch = 1 << l;
+    gemmT(g);
+  }
+  void dgemm_nodes(int np, int w2, const T* a, const T* b, T* cc) {
+    GemmArgs g;
+    g.M = w2; g.N = w2; g.K = w2;
+    g.A = a; g.lda = w2; g.sA = (long long)w2 * w2;
+    g.B = b; g.ldb = w2; g.sB = (long long)w2 * w2;
+    g.C = cc; g.ldc = w2; g.sC = (long long)w2 * w2; g.batch = np;
+    gemmT(g);
+  }
+  void sum_doubles_scaled(double* x, int n, double* out, double scale);
+
+  void traces(double* t, double* f) override {
+    if (!built) throw Error(HODLR_EINVAL, "no build");
+    traces_impl(true, t, f);
+  }
+
+  // ---------------------------------------------------------------- likelihood, gradient, Fisher
+  void eval(const double* theta, const double* y, double* nll, double* grad, double* fisher) override {
+    bool same = built;
+    for (int k = 0; k < 4; ++k) same = same && theta[k] == theta_built[k];
+    if (!same) build(theta);
+    const double s2 = theta[0], t2 = theta[3];
+    double a_y = 0.0, a_a = 0.0, aKa[2] = {0, 0};
+    if (nll || grad) {
+      if (!y) throw Error(HODLR_EINVAL, "y is required");
+      HODLR_CUDA(cudaMemsetAsync(d_status + 1, 0, sizeof(int), st));
+      check_finite<double>(y, N, d_status + 1, st);
+      permute_rows<double, double>(y, N, vec_d, N, d_perm_plain, N, 1, 0, st);   // y in tree order
+      solve_tree(vec_d, vec_d + N);                                               // alpha
+      double* alpha = vec_d + N;
+      dot_columns<double, double>(N, 1, vec_d, N, alpha, N, res + 40, st);        // y^T alpha
+      dot_columns<double, double>(N, 1, alpha, N, alpha, N, res + 41, st);        // alpha^T alpha
+      if (grad) {
+        for (int j = 0; j < 2; ++j) {
+          matvec<double>(j, alpha, N, vec_d2, N, 1, 0);
+          dot_columns<double, double>(N, 1, alpha, N, vec_d2, N, res + 42 + j, st);
+        }
+      }
+      double h[4];
+      int bad = 0;
+      HODLR_CUDA(cudaMemcpyAsync(h, res + 40, sizeof(h), cudaMemcpyDeviceToHost, st));
+      HODLR_CUDA(cudaMemcpyAsync(&bad, d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+      HODLR_CUDA(cudaStreamSynchronize(st));
+      if (bad) throw Error(HODLR_ENUMERIC, "y has NaN or Inf");
+      a_y = h[0]; a_a = h[1]; aKa[0] = h[2]; aKa[1] = h[3];
+    }
+    double t[3] = {0, 0, 0}, f[9] = {0};
+    if (grad || fisher) traces_impl(fisher != nullptr, t, f);
+    const double n = (double)N;
+    double out_nll = 0.5 * n * log(2.0 * M_PI) + 0.5 * logdet + 0.5 * a_y;
+    // traces of K~^{-1} K~_j: sigma2 -> (N - tau2 t0)/sigma2, ell -> t1, kappa -> t2, tau2 -> t0
+    double trj[4] = {(n - t2 * t[0]) / s2, t[1], t[2], t[0]};
+    double quad[4] = {(a_y - t2 * a_a) / s2, aKa[0], aKa[1], a_a};
+    if (nll) *nll = out_nll;
+    if (grad)
+      for (int j = 0; j < 4; ++j) grad[j] = 0.5 * trj[j] - 0.5 * quad[j];
+    if (fisher) {
+      // F_ab = tr(K~^{-1} M_a K~^{-1} M_b) for M in (I, K_ell, K_kappa): f[3a+b]
+      // K~_sigma2 = (K~ - tau2 I)/sigma2:
+      //   tr(K^-1 Ks K^-1 M) = (t_M - tau2 f_{0M})/sigma2,  tr(K^-1 Ks K^-1 Ks) = (N - 2 tau2 t0 + tau2^2 f00)/sigma2^2
+      auto F3 = [&](int a, int b) { return f[3 * a + b]; };
+      double I4[4][4];
+      int map[4] = {-1, 1, 2, 0};   // parameter -> index in (I, ell, kappa); -1 = sigma2
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          int ia = map[a], ib = map[b];
+          double v;
+          if (ia < 0 && ib < 0) v = (n - 2.0 * t2 * t[0] + t2 * t2 * F3(0, 0)) / (s2 * s2);
+          else if (ia < 0) v = (t[ib] - t2 * F3(0, ib)) / s2;
+          else if (ib < 0) v = (t[ia] - t2 * F3(0, ia)) / s2;
+          else v = F3(ia, ib);
+          I4[a][b] = 0.5 * v;
+        }
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) fisher[4 * a + b] = I4[a][b];
+    }
+    bool fin = std::isfinite(out_nll);
+    if (grad) for (int j = 0; j < 4; ++j) fin = fin && std::isfinite(grad[j]);
+    if (fisher) for (int j = 0; j < 16; ++j) fin = fin && std::isfinite(fisher[j]);
+    if (!fin) throw Error(HODLR_ENUMERIC, "non-finite result");
+  }
+
+  // ---------------------------------------------------------------- test entry points
+  void apply_nat(const double* theta, int which, const double* X, double* Yo, int ncols) override {
+    for (int k = 0; k < 4; ++k) theta_built[k] = theta[k];
+    built = false;
+    set_physics(theta);
+    // natural -> tree (T), apply, tree -> natural (double)
+    for (int c0 = 0; c0 < ncols; c0 += c) {
+      int qq = std::min(c, ncols - c0);
+      permute_rows<double, T>(X + (size_t)c0 * N, N, R, N, d_perm_plain, N, qq, 0, st);
+      T* o = KR;
+      if (which == 0) apply(R, N, qq, o, nullptr, nullptr, N);
+      else if (which == 2) apply(R, N, qq, nullptr, o, nullptr, N);
+      else if (which == 3) apply(R, N, qq, nullptr, nullptr, o, N);
+      else if (which == 1) {
+        apply(R, N, qq, o, nullptr, nullptr, N);
+        axpby<T>(N, qq, -theta[3] / theta[0], R, N, 1.0 / theta[0], o, N, st);
+      } else if (which == 4) {
+        HODLR_CUDA(cudaMemcpyAsync(o, R, sizeof(T) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
+      } else throw Error(HODLR_EINVAL, "which");
+      permute_rows<T, double>(o, N, Yo + (size_t)c0 * N, N, d_perm_plain, N, qq, 1, st);
+    }
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+  void probe(int level, int ncols, double* out) override {
+    if (level < 1 || level > tau || ncols > c) throw Error(HODLR_EINVAL, "level / ncols");
+    probe_panel<T>(N, ncols, level, 0, seed, d_mask[level], R, N, st);
+    convert<T, double>(R, out, (long long)N * ncols, st);
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+  void densify(int which, double* out) override {
+    if (!built) throw Error(HODLR_EINVAL, "no build");
+    if ((long long)N * N > (1LL << 28)) throw Error(HODLR_EINVAL, "densify is for small N only");
+    // columns of the identity through the HODLR product
+    int j = which == 0 || which == 1 || which == 4 ? -1 : which - 2;
+    const int qd = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)wide * sizeof(T) / sizeof(double)));
+    for (int c0 = 0; c0 < N; c0 += qd) {
+      int qq = std::min(qd, N - c0);
+      double* col = out + (size_t)c0 * N;
+      fill<double>(col, 0.0, (long long)N * qq, st);
+      set_unit(col, c0, qq);
+      HODLR_CUDA(cudaMemcpyAsync(WZ, col, sizeof(double) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
+      matvec<double>(j, (const double*)WZ, N, col, N, qq, 0);
+      if (which == 1) axpby<double>(N, qq, -theta_built[3] / theta_built[0], (const double*)WZ, N,
+                                    1.0 / theta_built[0], col, N, st);
+      if (which == 4) HODLR_CUDA(cudaMemcpyAsync(col, WZ, sizeof(double) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
+    }
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+  void set_unit(double* col, int c0, int qq);
+  void solve_nat(const double* b, double* x) override {
+    if (!built) throw Error(HODLR_EINVAL, "no build");
+    permute_rows<double, double>(b, N, vec_d, N, d_perm_plain, N, 1, 0, st);
+    solve_tree(vec_d, vec_d + N);
+    permute_rows<double, double>(vec_d + N, N, x, N, d_perm_plain, N, 1, 1, st);
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+  void set_pivots(const int32_t* piv) override {
+    if (!piv) { frozen = false; return; }
+    size_t off = 0;
+    for (int l = 1; l <= tau; ++l) {
+      HODLR_CUDA(cudaMemcpyAsync(d_piv[l], piv + off, sizeof(int) * (size_t)npairs(l) * c, cudaMemcpyHostToDevice, st));
+      off += (size_t)npairs(l) * c;
+    }
+    HODLR_CUDA(cudaStreamSynchronize(st));
+    frozen = true;
+    built = false;
+  }
+  void get_pivots(int32_t* piv) const override {
+    size_t off = 0;
+    for (int l = 1; l <= tau; ++l) {
+      HODLR_CUDA(cudaMemcpy(piv + off, d_piv[l], sizeof(int) * (size_t)npairs(l) * c, cudaMemcpyDeviceToHost));
+      off += (size_t)npairs(l) * c;
+    }
+  }
+};
+
+// small kernels local to the engine
+namespace {
+template <class T>
+__global__ void identity_blocks_kernel(const int* bounds, int nl, T* S, long long ld) {
+  int b = blockIdx.x;
+  int lo = bounds[b], n = bounds[b + 1] - lo;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S[lo + i + (size_t)i * ld] = T(1);
+}
+__global__ void unit_cols_kernel(double* col, long long N, int c0, int qq) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < qq) col[c0 + j + (size_t)j * N] = 1.0;
+}
+__global__ void scale_sum_kernel(const double* x, int n, double* out, double scale) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    *out += scale * t;
+  }
+}
+}  // namespace
+
+template <class T> void Engine<T>::identity_blocks(T* Sl) {
+  identity_blocks_kernel<T><<<nleaves, 256, 0, st>>>(d_leafb, leaf, Sl, N);
+  check_launch("identity_blocks");
+}
+template <class T> void Engine<T>::set_unit(double* col, int c0, int qq) {
+  unit_cols_kernel<<<cdiv(qq, 64), 64, 0, st>>>(col, N, c0, qq);
+  check_launch("unit_cols");
+}
+template <class T> void Engine<T>::sum_doubles_scaled(double* x, int n, double* out, double scale) {
+  scale_sum_kernel<<<1, 1024, 0, st>>>(x, n, out, scale);
+  check_launch("scale_sum");
+}
+
+template struct Engine<double>;
+template struct Engine<float>;
+
+}  // namespace hodlr
+
+// ================================================================================ C ABI
+using namespace hodlr;
+
+struct hodlr_ctx {
+  Base* e = nullptr;
+  std::string err;
+};
+
+template <class F> static int guarded(hodlr_ctx* h, F f) {
+  if (!h || !h->e) return HODLR_EINVAL;
+  try {
+    f();
+    h->err.clear();
+    return HODLR_OK;
+  } catch (const Error& x) {
+    h->err = x.what();
+    cudaGetLastError();
+    return x.code;
+  } catch (const std::exception& x) {
+    h->err = x.what();
+    return HODLR_EINVAL;
+  }
+}
+
+static Base* make_engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t st) {
+  if (m->precision == HODLR_FP64) return new Engine<double>(m, o, st);
+  if (m->precision == HODLR_MIXED_FP32) return new Engine<float>(m, o, st);
+  throw Error(HODLR_EINVAL, "precision");
+}
+
+template <class T> static size_t plan_bytes(Engine<T>* e) {
+  Arena ar;
+  ar.plan = true;
+  e->carve(ar);
+  return ar.off + 4096;
+}
+
+extern "C" {
+
+size_t hodlr_workspace_size(const hodlr_model* m, const hodlr_opts* o) {
+  if (!m || !o) return 0;
+  try {
+    Base* b = make_engine(m, o, nullptr);
+    size_t s = 0;
+    if (auto* d = dynamic_cast<Engine<double>*>(b)) s = plan_bytes(d);
+    else if (auto* f = dynamic_cast<Engine<float>*>(b)) s = plan_bytes(f);
+    delete b;
+    return s;
+  } catch (...) {
+    return 0;
+  }
+}
+
+int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, void* cuda_stream, void* workspace,
+                 size_t workspace_bytes) {
+  if (!out || !m || !o) return HODLR_EINVAL;
+  *out = nullptr;
+  hodlr_ctx* h = new hodlr_ctx;
+  try {
+    h->e = make_engine(m, o, (cudaStream_t)cuda_stream);
+    Arena ar;
+    ar.plan = false;
+    ar.base = (char*)workspace;
+    ar.cap = workspace_bytes;
+    if (!workspace || ((uintptr_t)workspace & 255)) throw Error(HODLR_EINVAL, "workspace must be 256-byte aligned");
+    if (auto* d = dynamic_cast<Engine<double>*>(h->e)) { d->carve(ar); d->upload_tree(); }
+    else if (auto* f = dynamic_cast<Engine<float>*>(h->e)) { f->carve(ar); f->upload_tree(); }
+  } catch (const Error& x) {
+    int code = x.code;
+    delete h->e;
+    delete h;
+    return code;
+  } catch (...) {
+    delete h->e;
+    delete h;
+    return HODLR_EINVAL;
+  }
+  *out = h;
+  return HODLR_OK;
+}
+
+int hodlr_build(hodlr_ctx* h, const double* theta, const double* points) {
+  if (points) return HODLR_ENOTIMPL;
+  if (!theta) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->build(theta); });
+}
+int hodlr_nll(hodlr_ctx* h, const double* theta, const double* y, double* nll_out) {
+  if (!theta || !y || !nll_out) return HODLR_EINVAL;
+  return guarded(h, [&] { double v; h->e->eval(theta, y, &v, nullptr, nullptr); *nll_out = v; });
+}
+int hodlr_grad(hodlr_ctx* h, const double* theta, const double* y, double* grad_out) {
+  if (!theta || !y || !grad_out) return HODLR_EINVAL;
+  return guarded(h, [&] { double g[4]; h->e->eval(theta, y, nullptr, g, nullptr); std::memcpy(grad_out, g, sizeof(g)); });
+}
+int hodlr_fisher(hodlr_ctx* h, const double* theta, double* fisher_out) {
+  if (!theta || !fisher_out) return HODLR_EINVAL;
+  return guarded(h, [&] { double f[16]; h->e->eval(theta, nullptr, nullptr, nullptr, f); std::memcpy(fisher_out, f, sizeof(f)); });
+}
+int hodlr_eval(hodlr_ctx* h, const double* theta, const double* y, double* nll_out, double* grad_out,
+               double* fisher_out) {
+  if (!theta) return HODLR_EINVAL;
+  return guarded(h, [&] {
+    double v, g[4], f[16];
+    h->e->eval(theta, y, nll_out ? &v : nullptr, grad_out ? g : nullptr, fisher_out ? f : nullptr);
+    if (nll_out) *nll_out = v;
+    if (grad_out) std::memcpy(grad_out, g, sizeof(g));
+    if (fisher_out) std::memcpy(fisher_out, f, sizeof(f));
+  });
+}
+int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, const double* const* ys, double* nll_out,
+                         double* grad_out) {
+  if (!hs || nb <= 0 || !thetas || !ys || !nll_out || !grad_out) return HODLR_EINVAL;
+  for (int i = 0; i < nb; ++i) {
+    int rc = guarded(hs[i], [&] {
+      double v, g[4];
+      hs[i]->e->eval(thetas + 4 * i, ys[i], &v, g, nullptr);
+      nll_out[i] = v;
+      std::memcpy(grad_out + 4 * i, g, sizeof(g));
+    });
+    if (rc) return rc;
+  }
+  return HODLR_OK;
+}
+int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out) {
+  if (!h || !h->e || !perm_out) return HODLR_EINVAL;
+  std::memcpy(perm_out, h->e->perm64.data(), sizeof(int64_t) * h->e->N);
+  return HODLR_OK;
+}
+int hodlr_dims(const hodlr_ctx* h, int64_t* out) {
+  if (!h || !h->e || !out) return HODLR_EINVAL;
+  out[0] = h->e->N; out[1] = h->e->tau; out[2] = h->e->leaf; out[3] = h->e->c; out[4] = h->e->cap;
+  out[5] = h->e->nleaves;
+  return HODLR_OK;
+}
+int hodlr_ranks(const hodlr_ctx* h, int32_t* ranks_out) {
+  if (!h || !h->e || !ranks_out) return HODLR_EINVAL;
+  size_t off = 0;
+  for (int l = 1; l <= h->e->tau; ++l) {
+    const auto& r = h->e->host_rank[l];
+    for (size_t p = 0; p < (size_t)(1 << (l - 1)); ++p) ranks_out[off++] = p < r.size() ? r[p] : 0;
+  }
+  return HODLR_OK;
+}
+int hodlr_get_pivots(const hodlr_ctx* h, int32_t* piv_out) {
+  if (!h || !h->e || !piv_out) return HODLR_EINVAL;
+  try { h->e->get_pivots(piv_out); } catch (const Error& x) { return x.code; }
+  return HODLR_OK;
+}
+int hodlr_set_pivots(hodlr_ctx* h, const int32_t* piv_in) {
+  return guarded(h, [&] { h->e->set_pivots(piv_in); });
+}
+int hodlr_apply(hodlr_ctx* h, const double* theta, int which, const double* X, double* Yo, int ncols) {
+  if (!theta || !X || !Yo || ncols < 0 || which < 0 || which > 4) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->apply_nat(theta, which, X, Yo, ncols); });
+}
+int hodlr_probe(hodlr_ctx* h, int level, int ncols, double* out) {
+  if (!out) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->probe(level, ncols, out); });
+}
+int hodlr_densify(hodlr_ctx* h, int which, double* out) {
+  if (!out || which < 0 || which > 4) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->densify(which, out); });
+}
+int hodlr_solve(hodlr_ctx* h, const double* b, double* x) {
+  if (!b || !x) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->solve_nat(b, x); });
+}
+int hodlr_logdet(hodlr_ctx* h, double* logdet_out) {
+  if (!logdet_out) return HODLR_EINVAL;
+  return guarded(h, [&] {
+    if (!h->e->built) throw Error(HODLR_EINVAL, "no build");
+    *logdet_out = h->e->logdet;
+  });
+}
+int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out) {
+  if (!t_out || !f_out) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->traces(t_out, f_out); });
+}
+int hodlr_napply(const hodlr_ctx* h, int64_t* out) {
+  if (!h || !h->e || !out) return HODLR_EINVAL;
+  *out = h->e->napply;
+  return HODLR_OK;
+}
+int hodlr_kernel_count(const hodlr_ctx* h, int64_t* out) {
+  if (!h || !out) return HODLR_EINVAL;
+  *out = g_kernel_launches;
+  return HODLR_OK;
+}
+int hodlr_reset_kernel_count(hodlr_ctx* h) {
+  if (!h) return HODLR_EINVAL;
+  g_kernel_launches = 0;
+  return HODLR_OK;
+}
+const char* hodlr_last_error(const hodlr_ctx* h) { return h ? h->err.c_str() : "null context"; }
+void hodlr_destroy(hodlr_ctx* h) {
+  if (!h) return;
+  delete h->e;
+  delete h;
+}
+
+}  // extern "C"

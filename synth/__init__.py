@@ -28,7 +28,12 @@ import scipy.fft
 import scipy.linalg
 
 __all__ = ["Workload", "WORKLOADS", "workload", "simulate_y", "batched_draws",
-           "small_workload"]
+           "small_workload", "GUARD"]
+
+# Rank guard of the pivoted QR per arithmetic precision (a block keeps the leading
+# |R_ii| > max(tol, guard) |R_11|).  Alg. 2 multiplies rounding in the kept directions by
+# cond(R) <= 1/guard, so the guard sets the accuracy of the derivative matrices.
+GUARD = {"fp64": 1e-5, "fp32": 1e-3}
 
 
 @dataclasses.dataclass(frozen=True)

@@ -1,0 +1,72 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of include/hodlr.h.
+
+No compute calls: this runs on machines without a GPU.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import synth
+from paper_2303_10102_gb300 import build as pbuild
+from paper_2303_10102_gb300 import lib as plib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hodlr.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hodlr_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def so_path():
+    return pbuild.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ["hodlr_create", "hodlr_build", "hodlr_nll", "hodlr_grad", "hodlr_fisher",
+                     "hodlr_batch_nll_grad", "hodlr_perm", "hodlr_last_error", "hodlr_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(so_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", so_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (hodlr_[a-z_0-9]+)\b", out))
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(so_path)
+    for n in declared_symbols():
+        assert getattr(lib, n) is not None
+    assert set(plib.SIGNATURES) == set(declared_symbols())
+
+
+def test_build_targets_sm_103a_only():
+    assert "arch=compute_103a,code=sm_103a" in pbuild.FLAGS
+    assert sum("arch=" in f for f in pbuild.FLAGS) == 1
+
+
+@pytest.mark.parametrize("name", ["C0", "C1", "C2", "C4"])
+def test_workspace_plan(so_path, name):
+    w = synth.workload(name)
+    lib = plib.load()
+    m = plib.Model(w.dim, (ctypes.c_int * 2)(w.G, w.G if w.dim == 2 else 1), w.nvar, w.nu, 1)
+    o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1)
+    n = lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o))
+    assert n > 0
+    assert n < 280 * 2 ** 30, n / 2 ** 30          # fits one GB300 (FP32 bulk)
+
+
+def test_workspace_plan_rejects_bad_options(so_path):
+    lib = plib.load()
+    m = plib.Model(3, (ctypes.c_int * 2)(8, 8), 1, 1.5, 0)
+    o = plib.Opts(16, 4, 0, 0.0, 1)
+    assert lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o)) == 0
+    m = plib.Model(1, (ctypes.c_int * 2)(64, 1), 2, 1.5, 0)
+    o = plib.Opts(15, 4, 0, 0.0, 1)                # leaf not a multiple of nvar
+    assert lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o)) == 0
