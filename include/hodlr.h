@@ -73,8 +73,9 @@ typedef struct {
  *   oversample  probe columns c = rank_or_cap + oversample
  *   tol         relative truncation tolerance of the pivoted QR (0 = fixed rank);
  *               a block keeps the leading |R_ii| > max(tol, guard) |R_11|, guard =
- *               1e-5 (FP64) or 1e-3 (mixed).  The guard bounds cond(R) and with it the
- *               rounding amplification of the differentiated QR (Alg. 2).
+ *               1e-5.  The guard bounds cond(R) and with it the rounding amplification
+ *               of the differentiated QR (Alg. 2): derivative matrices carry errors of
+ *               order u * cond(R) (u = unit roundoff of the sketch arithmetic).
  *   seed        Philox key of the probes (fixed across theta, Sec. 3.3)            */
 typedef struct {
   int leaf;
@@ -163,6 +164,16 @@ int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out);
 
 /* Number of K or K_j vector products (columns) of the last build (Sec. 3.2.2 count).  */
 int hodlr_napply(const hodlr_ctx* h, int64_t* out);
+
+/* Kernel-time profile of the dense contraction kernel (the batched GEMM that carries the
+ * peeling, projection, factorization and trace products).  hodlr_profile(h, 1) records a
+ * pair of CUDA events on the context's stream around every GEMM launch from then on;
+ * hodlr_profile_read(h, out) synchronises and returns out[0] = total kernel milliseconds,
+ * out[1] = launches, out[2] = algorithmic flops (2 M N K per matrix product),
+ * out[3] = algorithmic operand bytes (each of A, B read once and C written once);
+ * hodlr_profile(h, 0) stops and clears.  Event pool: 65536 launches.  */
+int hodlr_profile(hodlr_ctx* h, int enable);
+int hodlr_profile_read(hodlr_ctx* h, double* out);
 
 /* Launch statistics: number of kernels launched since the last reset (host int64).  */
 int hodlr_kernel_count(const hodlr_ctx* h, int64_t* out);

@@ -24,6 +24,15 @@ struct Error : std::runtime_error {
 
 // Kernel-launch counter (per process); every launcher bumps it.
 extern long long g_kernel_launches;
+
+// Optional event profile of the GEMM launches (see hodlr_profile in hodlr.h).
+struct GemmProfile {
+  bool on = false;
+  cudaEvent_t* ev = nullptr;   // 2 per launch
+  int cap = 0, n = 0;
+  double flops = 0.0, bytes = 0.0;
+};
+extern GemmProfile g_prof;
 inline void count_launch(int n = 1) { g_kernel_launches += n; }
 
 inline void check_launch(const char* what) {

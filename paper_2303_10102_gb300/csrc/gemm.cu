@@ -12,6 +12,7 @@
 namespace hodlr {
 
 long long g_kernel_launches = 0;
+GemmProfile g_prof;
 
 namespace {
 
@@ -162,8 +163,18 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (g.K <= 0) kchunk = 0;
   dim3 grid(cdiv(g.M, BM), cdiv(g.N, BN), g.batch * nsplit);
   if (grid.z > 65535) throw Error(-1, "gemm: batch too large");
+  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
   gemm_kernel<TA, TB, TC, Acc><<<grid, NT, 0, st>>>(g, nsplit, kchunk, (Acc*)s.ptr);
   check_launch("gemm_kernel");
+  if (prof) {
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    ++g_prof.n;
+    double mnk = (double)g.M * g.N * g.K * g.batch;
+    g_prof.flops += 2.0 * mnk;
+    g_prof.bytes += ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
+                     (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch;
+  }
   if (nsplit > 1) {
     long long mn = (long long)g.M * g.N;
     dim3 rg(cdiv(mn, 256), g.batch);
@@ -179,5 +190,7 @@ template void gemm<float, double, double, double>(const GemmArgs&, Scratch, cuda
 template void gemm<double, float, float, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm<double, double, float, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm<float, float, float, double>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm<double, float, float, float>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm<double, float, double, double>(const GemmArgs&, Scratch, cudaStream_t);
 
 }  // namespace hodlr

@@ -85,7 +85,8 @@ struct Engine : Base {
   std::vector<unsigned char*> d_mask;    // per level (1..tau): right-child rows
   int* d_leafb = nullptr;
   // level data
-  std::vector<T*> F, U, CP, dF[2];
+  std::vector<T*> F, CP, dF[2];
+  std::vector<double*> U, CP64;        // FP64 factorization data (App. C)
   std::vector<int*> d_rank, d_piv;
   std::vector<double*> d_nodelog;
   std::vector<int> w;                    // width per level
@@ -115,7 +116,8 @@ struct Engine : Base {
   T *tpan = nullptr;                    // peel T blocks
   double *vec_d = nullptr, *vec_d2 = nullptr, *vec_d3 = nullptr, *red = nullptr, *res = nullptr;
   T* vec_t = nullptr;
-  double* Afp = nullptr;
+  double* Afp = nullptr;                // FP64 leaf blocks, then their Cholesky factors
+  double *sgbuf = nullptr, *fg64 = nullptr, *stb64 = nullptr;
   int* d_status = nullptr;
   Scratch scratch;
   // state
@@ -127,7 +129,7 @@ struct Engine : Base {
   Engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t s_) {
     dim = m->dim; G = m->grid[0]; nvar = m->nvar; nu = m->nu; prec = m->precision;
     leaf = o->leaf; cap = o->rank_or_cap; c = o->rank_or_cap + o->oversample; tol = o->tol; seed = o->seed;
-    guard = prec == HODLR_FP64 ? 1e-5 : 1e-3;
+    guard = 1e-5;
     st = s_;
     if (dim < 1 || dim > 2 || nvar < 1 || nvar > 2 || G < 2 || leaf < nvar || leaf % nvar || cap < 1 || c < cap ||
         (nu != 0.5 && nu != 1.5))
@@ -205,6 +207,8 @@ struct Engine : Base {
   int npairs(int l) const { return 1 << (l - 1); }
   int msize(int d) const { return bnd[d][1] - bnd[d][0]; }  // node size at depth d
 
+  static T* plan_or(T* base, size_t off) { return base ? base + off : nullptr; }
+
   // ---------------------------------------------------------------- workspace plan / carve
   void carve(Arena& ar) {
     const size_t NN = (size_t)N;
@@ -215,15 +219,16 @@ struct Engine : Base {
     d_mask.assign(tau + 1, nullptr);
     for (int l = 1; l <= tau; ++l) d_mask[l] = ar.take<unsigned char>(N);
     d_leafb = ar.take<int>(nleaves + 1);
-    F.assign(tau + 1, nullptr); U.assign(tau + 1, nullptr); CP.assign(tau + 1, nullptr);
+    F.assign(tau + 1, nullptr); U.assign(tau + 1, nullptr); CP.assign(tau + 1, nullptr); CP64.assign(tau + 1, nullptr);
     dF[0].assign(tau + 1, nullptr); dF[1].assign(tau + 1, nullptr);
     d_rank.assign(tau + 1, nullptr); d_piv.assign(tau + 1, nullptr); d_nodelog.assign(tau + 1, nullptr);
     for (int l = 1; l <= tau; ++l) {
       F[l] = ar.take<T>(NN * cap);
-      U[l] = ar.take<T>(NN * cap);
+      U[l] = ar.take<double>(NN * cap);
       dF[0][l] = ar.take<T>(NN * cap);
       dF[1][l] = ar.take<T>(NN * cap);
       CP[l] = ar.take<T>((size_t)npairs(l) * 4 * cap * cap);
+      CP64[l] = ar.take<double>((size_t)npairs(l) * 4 * cap * cap);
       d_rank[l] = ar.take<int>(npairs(l));
       d_piv[l] = ar.take<int>((size_t)npairs(l) * c);
       d_nodelog[l] = ar.take<double>(npairs(l));
@@ -271,11 +276,11 @@ struct Engine : Base {
     t3 = ar.take<double>((size_t)maxp * cap * cap);
     phi = ar.take<double>((size_t)maxp * cap * cap);
     // leaves / wide panels
-    for (int k = 0; k < 3; ++k) E[k] = ar.take<T>(NN * leaf);
     wide = std::max(nwide * cap, 3 * leaf);
     WP = ar.take<T>(NN * wide);
     WZ = ar.take<T>(NN * wide);
     LinvLeaf = ar.take<double>(nl2);
+    for (int k = 0; k < 3; ++k) E[k] = plan_or(WZ, (size_t)k * NN * leaf);
     size_t qmax = (size_t)wide;
     qmax = std::max<size_t>(qmax, (size_t)c);
     fg = ar.take<T>((size_t)maxb * cap * qmax);
@@ -289,7 +294,10 @@ struct Engine : Base {
     vec_t = ar.take<T>(NN * 2);
     red = ar.take<double>((size_t)std::max(maxb, nleaves) * 16 + 64);
     res = ar.take<double>(256);
-    Afp = ar.take<double>(std::max(nl2, (size_t)maxb * cap * cap));
+    Afp = ar.take<double>(nl2);
+    sgbuf = ar.take<double>((size_t)maxb * cap * cap);
+    fg64 = ar.take<double>((size_t)maxb * cap * cap);
+    stb64 = ar.take<double>((size_t)maxb * cap * cap);
     d_status = ar.take<int>(8);
     size_t sbytes = std::max<size_t>(64u << 20, (size_t)4 * c * c * 8 * 640);
     scratch.ptr = ar.take<char>(sbytes);
@@ -632,8 +640,10 @@ struct Engine : Base {
   // solve with the block-diagonal of the depth-d subtrees:  out = diag_v(K~_v^{-1}) in
   void solve_depth(const T* in, long long ldi, T* out, long long ldo, int q, int d) {
     const int nl = leaf;
-    {
-      GemmArgs g;
+    if (sizeof(T) == 8) {
+      leaf_trsm<T, T>(nleaves, nl, Afp, in, ldi, out, ldo, q, st);      // FP64: backward-stable leaf solves
+    } else {
+      GemmArgs g;                                                      // FP32 bulk: explicit A_b^{-1}
       g.M = nl; g.N = q; g.K = nl;
       g.A = Ainv; g.lda = nl; g.sA = (long long)nl * nl;
       g.B = in; g.ldb = ldi; g.sB = nl;
@@ -665,12 +675,43 @@ struct Engine : Base {
       k.B = stb; k.ldb = q; k.sB = (long long)q * wl; k.tB = 1;
       k.C = out; k.ldc = ldo; k.sC = m;
       k.alpha = -1.0; k.beta = 1.0; k.batch = nbk;
-      gemmT(k);
+      gemm<double, T, T, T>(k, scratch, st);
+    }
+  }
+
+  // FP64 solve with the depth-d subtrees (factorization sweeps and K~^{-1} y): leaf Cholesky
+  // solves and Woodbury corrections in FP64 against the stored factors F (App. C).
+  void solve64(const double* in, long long ldi, double* out, long long ldo, int q, int d) {
+    leaf_trsm<double, double>(nleaves, leaf, Afp, in, ldi, out, ldo, q, st);
+    for (int l = tau; l > d; --l) {
+      int wl = w[l];
+      if (wl == 0) continue;
+      int m = msize(l), np = npairs(l), nbk = 1 << l;
+      GemmArgs g;
+      g.M = q; g.N = wl; g.K = m;
+      g.A = out; g.lda = ldo; g.sA = m; g.tA = 1;
+      g.B = F[l]; g.ldb = N; g.sB = m;
+      g.C = fg64; g.ldc = q; g.sC = (long long)q * wl; g.batch = nbk;
+      gemm<double, T, double, double>(g, scratch, st);
+      GemmArgs h;
+      h.M = q; h.N = 2 * wl; h.K = 2 * wl;
+      h.A = fg64; h.lda = q; h.sA = 2LL * q * wl;
+      h.B = CP64[l]; h.ldb = 2 * wl; h.sB = 4LL * wl * wl; h.tB = 1;
+      h.C = stb64; h.ldc = q; h.sC = 2LL * q * wl; h.batch = np;
+      gemm<double, double, double, double>(h, scratch, st);
+      GemmArgs k;
+      k.M = m; k.N = q; k.K = wl;
+      k.A = U[l]; k.lda = N; k.sA = m;
+      k.B = stb64; k.ldb = q; k.sB = (long long)q * wl; k.tB = 1;
+      k.C = out; k.ldc = ldo; k.sC = m;
+      k.alpha = -1.0; k.beta = 1.0; k.batch = nbk;
+      gemm<double, double, double, double>(k, scratch, st);
     }
   }
 
   void factor() {
-    double* sg = Afp;  // Grams of the child blocks (FP64): even -> Sw, odd -> Sx
+    double* sg = sgbuf;  // Grams of the child blocks (FP64): even -> Sw, odd -> Sx
+    double* Fd = (double*)WZ;   // FP64 copy of a factor panel (N x wl)
     for (int l = tau; l >= 1; --l) {
       int wl = w[l];
       int np = npairs(l);
@@ -678,7 +719,8 @@ struct Engine : Base {
         fill<double>(d_nodelog[l], 0.0, np, st);
         continue;
       }
-      solve_depth(F[l], N, U[l], N, wl, l);
+      convert<T, double>(F[l], Fd, (long long)N * wl, st);
+      solve64(Fd, N, U[l], N, wl, l);                                     // [W~; X~] = K~_child^{-1} [W; X]
       {
         GemmArgs g;
         int m = msize(l);
@@ -686,7 +728,7 @@ struct Engine : Base {
         g.A = F[l]; g.lda = N; g.sA = m; g.tA = 1;
         g.B = U[l]; g.ldb = N; g.sB = m;
         g.C = sg; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = 1 << l;
-        gemm<T, T, double, double>(g, scratch, st);
+        gemm<T, double, double, double>(g, scratch, st);
       }
       const long long w2 = (long long)wl * wl;
       // split into Sw (even blocks) and Sx (odd blocks)
@@ -711,11 +753,12 @@ struct Engine : Base {
       shift_identity(np, wl, t3, wl, w2, 1.0, 1.0, st);                       // I + Sw Phi Sx
       // CP = C^{-1} P = [[-Phi Sx, Phi], [I + Sw Phi Sx, -Sw Phi]]  (2wl x 2wl)
       const long long s4 = 4 * w2, ld2 = 2 * wl;
-      T* cp = CP[l];
-      copy_blocks<double, T>(np, wl, wl, t1, wl, w2, cp, ld2, s4, -1.0, st);
-      copy_blocks<double, T>(np, wl, wl, phi, wl, w2, cp + wl * ld2, ld2, s4, 1.0, st);
-      copy_blocks<double, T>(np, wl, wl, t3, wl, w2, cp + wl, ld2, s4, 1.0, st);
-      copy_blocks<double, T>(np, wl, wl, t2, wl, w2, cp + wl + wl * ld2, ld2, s4, -1.0, st);
+      double* cp = CP64[l];
+      copy_blocks<double, double>(np, wl, wl, t1, wl, w2, cp, ld2, s4, -1.0, st);
+      copy_blocks<double, double>(np, wl, wl, phi, wl, w2, cp + wl * ld2, ld2, s4, 1.0, st);
+      copy_blocks<double, double>(np, wl, wl, t3, wl, w2, cp + wl, ld2, s4, 1.0, st);
+      copy_blocks<double, double>(np, wl, wl, t2, wl, w2, cp + wl + wl * ld2, ld2, s4, -1.0, st);
+      convert<double, T>(cp, CP[l], (long long)np * s4, st);
       status_check("SMW core");
     }
     // total log-det: leaves + nodes (Sylvester)
@@ -785,27 +828,10 @@ struct Engine : Base {
     }
   }
 
-  // ---------------------------------------------------------------- solve with refinement
-  // alpha = K~^{-1} b for a tree-order FP64 vector (FP64 path: direct; mixed: FP32 solve + FP64
-  // iterative refinement against the stored K~).
-  void solve_tree(const double* b, double* x) {
-    if (sizeof(T) == 8) {
-      solve_depth((const T*)b, N, (T*)x, N, 1, 0);
-      return;
-    }
-    // x0 = solve(b)
-    convert<double, T>(b, vec_t, N, st);
-    solve_depth(vec_t, N, (T*)vec_d3, N, 1, 0);
-    convert<T, double>((T*)vec_d3, x, N, st);
-    for (int it = 0; it < 3; ++it) {
-      matvec<double>(-1, x, N, vec_d2, N, 1, 0);                 // K~ x (FP64 vectors)
-      axpby<double>(N, 1, 1.0, b, N, -1.0, vec_d2, N, st);       // r = b - K~ x
-      convert<double, T>(vec_d2, vec_t, N, st);
-      solve_depth(vec_t, N, (T*)vec_d3, N, 1, 0);
-      convert<T, double>((T*)vec_d3, vec_d2, N, st);
-      axpby<double>(N, 1, 1.0, vec_d2, N, 1.0, x, N, st);
-    }
-  }
+  // ---------------------------------------------------------------- K~^{-1} b
+  // alpha = K~^{-1} b for a tree-order FP64 vector: FP64 solve against the stored K~ (its
+  // factors are exact in the stored precision, so no refinement is needed).
+  void solve_tree(const double* b, double* x) { solve64(b, N, x, N, 1, 0); }
 
   // ---------------------------------------------------------------- exact traces (App. B)
   // t[i] = tr(K~^{-1} M_i), f[i][j] = tr(K~^{-1} M_i K~^{-1} M_j), M = (I, K~_ell, K~_kappa)
@@ -845,8 +871,8 @@ struct Engine : Base {
       // WP = [P | Y1 | Y2 | Pi1 | Pi2]; P = U_v as a panel: c1 rows [W~, 0], c2 rows [0, X~]
       T* P = WP;
       fill<T>(P, T(0), pw, st);
-      copy_blocks<T, T>(np, m, wl, U[l], N, 2LL * m, P, N, 2LL * m, 1.0, st);
-      copy_blocks<T, T>(np, m, wl, U[l] + m, N, 2LL * m, P + m + (size_t)wl * N, N, 2LL * m, 1.0, st);
+      copy_blocks<double, T>(np, m, wl, U[l], N, 2LL * m, P, N, 2LL * m, 1.0, st);
+      copy_blocks<double, T>(np, m, wl, U[l] + m, N, 2LL * m, P + m + (size_t)wl * N, N, 2LL * m, 1.0, st);
       for (int i = 0; i < 2; ++i) matvec<T>(i, P, N, P + (size_t)(i + 1) * pw, N, w2, l - 1);
       int nsolve = 3;
       if (fisher) {
@@ -1314,6 +1340,43 @@ int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out) {
 int hodlr_napply(const hodlr_ctx* h, int64_t* out) {
   if (!h || !h->e || !out) return HODLR_EINVAL;
   *out = h->e->napply;
+  return HODLR_OK;
+}
+int hodlr_profile(hodlr_ctx* h, int enable) {
+  if (!h || !h->e) return HODLR_EINVAL;
+  try {
+    if (!g_prof.ev) {
+      g_prof.cap = 65536;
+      g_prof.ev = new cudaEvent_t[2 * g_prof.cap];
+      for (int i = 0; i < 2 * g_prof.cap; ++i) HODLR_CUDA(cudaEventCreate(&g_prof.ev[i]));
+    }
+    g_prof.n = 0;
+    g_prof.flops = g_prof.bytes = 0.0;
+    g_prof.on = enable != 0;
+  } catch (const Error& x) {
+    h->err = x.what();
+    return x.code;
+  }
+  return HODLR_OK;
+}
+int hodlr_profile_read(hodlr_ctx* h, double* out) {
+  if (!h || !h->e || !out) return HODLR_EINVAL;
+  try {
+    double ms = 0.0;
+    for (int i = 0; i < g_prof.n; ++i) {
+      HODLR_CUDA(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
+      float t = 0.f;
+      HODLR_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
+      ms += t;
+    }
+    out[0] = ms;
+    out[1] = g_prof.n;
+    out[2] = g_prof.flops;
+    out[3] = g_prof.bytes;
+  } catch (const Error& x) {
+    h->err = x.what();
+    return x.code;
+  }
   return HODLR_OK;
 }
 int hodlr_kernel_count(const hodlr_ctx* h, int64_t* out) {

@@ -75,6 +75,12 @@ void gather_columns(int nb, int m, long long row_stride, const T* Y, long long l
                     const int* rank, int w, T* dst, long long ldd, cudaStream_t st);
 // Alg. 2 core: M2 = skew(Yp) - Yp with skew(Y) = tril(Y,-1) - tril(Y,-1)^T (w x w per pair).
 template <class T> void alg2_core(int nb, int w, const T* Yp, T* M2, cudaStream_t st);
+// Leaf solves with the FP64 Cholesky factors: out_b = (L_b L_b^T)^{-1} in_b for every leaf b
+// (rows [b*nl, (b+1)*nl) of the panels, q columns).  Forward substitution by column sweeps,
+// backward substitution by warp dot products; backward stable, unlike an explicit inverse.
+template <class TI, class TO>
+void leaf_trsm(int nleaves, int nl, const double* L, const TI* in, long long ldi, TO* out, long long ldo, int q,
+               cudaStream_t st);
 // symmetrise and gather leaf blocks: A_b = (E_b + E_b^T)/2, E_b = E[rows of leaf b, 0:n_b]
 template <class TS, class TD>
 void extract_leaves(int nleaves, int nl, const int* bounds, const TS* E, long long lde, TD* A,

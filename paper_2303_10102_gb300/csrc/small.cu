@@ -529,3 +529,66 @@ template void axpby<double>(int, int, double, const double*, long long, double, 
 template void axpby<float>(int, int, double, const float*, long long, double, float*, long long, cudaStream_t);
 
 }  // namespace hodlr
+
+// ---------------------------------------------------------------- leaf triangular solves
+namespace hodlr {
+namespace {
+constexpr int TRSM_WARPS = 8;
+template <class TI, class TO>
+__global__ void __launch_bounds__(TRSM_WARPS * 32) leaf_trsm_kernel(int nl, const double* Lall, const TI* in,
+                                                                     long long ldi, TO* out, long long ldo, int q) {
+  extern __shared__ double xs[];   // TRSM_WARPS * nl
+  const int b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.y * TRSM_WARPS + warp;
+  const double* L = Lall + (size_t)b * nl * nl;
+  double* x = xs + (size_t)warp * nl;
+  const bool active = j < q;
+  if (active)
+    for (int i = lane; i < nl; i += 32) x[i] = (double)in[(size_t)b * nl + i + (size_t)j * ldi];
+  __syncwarp();
+  if (active) {
+    // forward: L y = b, column sweeps (L column-major, lower)
+    for (int i = 0; i < nl; ++i) {
+      double xi = x[i] / L[i + (size_t)i * nl];
+      __syncwarp();
+      if (lane == 0) x[i] = xi;
+      for (int k = i + 1 + lane; k < nl; k += 32) x[k] -= L[k + (size_t)i * nl] * xi;
+      __syncwarp();
+    }
+    // backward: L^T x = y, x_i = (y_i - sum_{k>i} L[k,i] x_k) / L[i,i]
+    for (int i = nl - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1 + lane; k < nl; k += 32) s += L[k + (size_t)i * nl] * x[k];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      s = __shfl_sync(0xffffffffu, s, 0);
+      double xi = (x[i] - s) / L[i + (size_t)i * nl];
+      __syncwarp();
+      if (lane == 0) x[i] = xi;
+      __syncwarp();
+    }
+    for (int i = lane; i < nl; i += 32) out[(size_t)b * nl + i + (size_t)j * ldo] = (TO)x[i];
+  }
+}
+}  // namespace
+
+template <class TI, class TO>
+void leaf_trsm(int nleaves, int nl, const double* L, const TI* in, long long ldi, TO* out, long long ldo, int q,
+               cudaStream_t st) {
+  if (nleaves <= 0 || q <= 0) return;
+  dim3 g(nleaves, cdiv(q, TRSM_WARPS));
+  size_t sm = (size_t)TRSM_WARPS * nl * sizeof(double);
+  if (sm > 48 * 1024)
+    HODLR_CUDA(cudaFuncSetAttribute(leaf_trsm_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  leaf_trsm_kernel<TI, TO><<<g, TRSM_WARPS * 32, sm, st>>>(nl, L, in, ldi, out, ldo, q);
+  check_launch("leaf_trsm");
+}
+template void leaf_trsm<double, double>(int, int, const double*, const double*, long long, double*, long long, int,
+                                        cudaStream_t);
+template void leaf_trsm<float, float>(int, int, const double*, const float*, long long, float*, long long, int,
+                                      cudaStream_t);
+template void leaf_trsm<float, double>(int, int, const double*, const float*, long long, double*, long long, int,
+                                       cudaStream_t);
+template void leaf_trsm<double, float>(int, int, const double*, const double*, long long, float*, long long, int,
+                                       cudaStream_t);
+}  // namespace hodlr

@@ -61,6 +61,8 @@ SIGNATURES = {
     "hodlr_logdet": (C.c_int, [_P, _D]),
     "hodlr_traces": (C.c_int, [_P, _D, _D]),
     "hodlr_napply": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "hodlr_profile": (C.c_int, [_P, C.c_int]),
+    "hodlr_profile_read": (C.c_int, [_P, _D]),
     "hodlr_kernel_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "hodlr_reset_kernel_count": (C.c_int, [_P]),
     "hodlr_last_error": (C.c_char_p, [_P]),
@@ -244,6 +246,14 @@ class Hodlr:
         v = np.zeros(1, dtype=np.int64)
         self._check(self.lib.hodlr_napply(self.h, v.ctypes.data_as(C.POINTER(C.c_int64))))
         return int(v[0])
+
+    def profile(self, enable):
+        self._check(self.lib.hodlr_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        out = np.zeros(4)
+        self._check(self.lib.hodlr_profile_read(self.h, _dp(out)))
+        return {"ms": float(out[0]), "launches": int(out[1]), "flops": float(out[2]), "bytes": float(out[3])}
 
     def kernel_count(self, reset=False):
         v = np.zeros(1, dtype=np.int64)

@@ -33,7 +33,10 @@ __all__ = ["Workload", "WORKLOADS", "workload", "simulate_y", "batched_draws",
 # Rank guard of the pivoted QR per arithmetic precision (a block keeps the leading
 # |R_ii| > max(tol, guard) |R_11|).  Alg. 2 multiplies rounding in the kept directions by
 # cond(R) <= 1/guard, so the guard sets the accuracy of the derivative matrices.
-GUARD = {"fp64": 1e-5, "fp32": 1e-3}
+# The truncation error must stay well below the nugget tau2 for K~ to remain positive
+# definite (leaf extraction sums every block's truncation error into the leaves), which
+# rules out large guards; both precisions use 1e-5.
+GUARD = {"fp64": 1e-5, "fp32": 1e-5}
 
 
 @dataclasses.dataclass(frozen=True)
