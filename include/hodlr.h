@@ -179,6 +179,24 @@ int hodlr_profile_read(hodlr_ctx* h, double* out);
 int hodlr_kernel_count(const hodlr_ctx* h, int64_t* out);
 int hodlr_reset_kernel_count(hodlr_ctx* h);
 
+/* Allocation-free physics product (the paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- code running inside another
+ * framework's memory pool or under a hard memory budget, or at a point where the
+ * allocator must not be called).  Computes Y = K X for the 1-D univariate model
+ * (K = A^{-1} K_u A^{-1} + tau2 I on G interior points, Matern nu = 0.5 or 1.5) without a
+ * context and without any workspace: X and Y are device arrays of G x ncols doubles,
+ * column-major, natural order; theta is a host array of 4 doubles; cuda_stream may be
+ * NULL.  Y may not alias X.
+ *   Limit: G <= 2048; larger grids return HODLR_EINVAL.
+ *   Scratch: a fixed 160.5 KiB array in device global memory, held by every GPU that loads
+ *   the library until the process exits.  The first call on a device looks its address up
+ *   (with that device current); make that first call before any stream capture.  All calls
+ *   share the one array, so calls that overlap on the GPU (other streams or host threads)
+ *   race and must be serialised by the caller.
+ *   Allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.  */
+int hodlr_apply_static(int G, double nu, const double* theta, const double* X, double* Y, int ncols,
+                       void* cuda_stream);
+
 const char* hodlr_last_error(const hodlr_ctx* h);
 void hodlr_destroy(hodlr_ctx* h);
 
