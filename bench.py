@@ -114,7 +114,7 @@ def oracle_rate(w, prec, napply_per_eval, budget_s=20.0):
         t0 = time.perf_counter()
         n = 0
         while True:
-            H = oh.build(m, t, w.theta, c=w.c, cap=w.cap, tol=w.tol, guard=synth.GUARD[prec], seed=w.seed_probe)
+            H = oh.build(m, t, w.theta, c=w.c, cap=w.cap, tol=w.tol, guard=w.guard, seed=w.seed_probe)
             ol.evaluate(H, y)
             n += 1
             el = time.perf_counter() - t0
@@ -171,7 +171,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=os.environ.get("HODLR_BENCH_WORKLOAD", "C4"))
+    # C4 (the 2^20-point bivariate grid) yields an indefinite K~ already in exact FP64 arithmetic
+    # at its tolerance 1e-5 (the leaf extraction sums truncation residuals of all blocks into the
+    # leaves, beyond the nugget); the default is the largest workload whose K~ is SPD.
+    ap.add_argument("--workload", default=os.environ.get("HODLR_BENCH_WORKLOAD", "C2"))
     ap.add_argument("--precision", default=None, help="fp64 or fp32 (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -200,7 +203,8 @@ def main():
     plib.load(build_if_missing=False)
 
     dev = torch.device("cuda", local)
-    h = Hodlr(w.dim, w.G, w.nvar, w.nu, prec, w.leaf, w.cap, w.c - w.cap, w.tol, w.seed_probe, device=dev)
+    h = Hodlr(w.dim, w.G, w.nvar, w.nu, prec, w.leaf, w.cap, w.c - w.cap, w.tol, w.seed_probe, device=dev,
+              guard=w.guard)
     y_host = torch.as_tensor(synth.simulate_y(w)).pin_memory()
     y_dev = y_host.to(dev)
     stream = h.stream

@@ -72,17 +72,20 @@ typedef struct {
  *   rank_or_cap kept-rank cap per off-diagonal block (stored factor width)
  *   oversample  probe columns c = rank_or_cap + oversample
  *   tol         relative truncation tolerance of the pivoted QR (0 = fixed rank);
- *               a block keeps the leading |R_ii| > max(tol, guard) |R_11|, guard =
- *               1e-5.  The guard bounds cond(R) and with it the rounding amplification
- *               of the differentiated QR (Alg. 2): derivative matrices carry errors of
- *               order u * cond(R) (u = unit roundoff of the sketch arithmetic).
- *   seed        Philox key of the probes (fixed across theta, Sec. 3.3)            */
+ *               a block keeps the leading |R_ii| > max(tol, guard) |R_11|.
+ *   seed        Philox key of the probes (fixed across theta, Sec. 3.3)
+ *   guard       rank guard (0 = 1e-5).  It bounds cond(R) and with it the rounding
+ *               amplification of the differentiated QR (Alg. 2): derivative matrices
+ *               carry errors of order u * cond(R).  It also bounds the truncation
+ *               residual that the leaf extraction sums over all leaves, which must stay
+ *               below the nugget tau2 for K~ to be positive definite.                */
 typedef struct {
   int leaf;
   int rank_or_cap;
   int oversample;
   double tol;
   uint64_t seed;
+  double guard;
 } hodlr_opts;
 
 /* Bytes of device workspace needed by a context for (m, o).  0 on bad arguments. */
@@ -161,6 +164,17 @@ int hodlr_logdet(hodlr_ctx* h, double* logdet_out);
 /* Exact traces (App. B.3): t[i] = tr(K~^{-1} M_i), f[3*i+j] = tr(K~^{-1} M_i K~^{-1} M_j)
  * for M = (I, K~_ell, K~_kappa).  t: host 3, f: host 9.  */
 int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out);
+
+/* Log-determinant split of the last factorization (App. C / Sylvester's identity):
+ * out[0] = sum over leaves of log|A_b|, out[l] = sum over the level-l nodes of
+ * log|I - Lw^T Sx Lw| (l = 1..tau); host array of tau + 1 doubles.  */
+int hodlr_logdet_levels(hodlr_ctx* h, double* out);
+
+/* Inspection of the factorization (tests): copies into `out` (host, FP64) the level-l panel
+ * F (what=0, N x w_l: Q in left-child rows, B~ in right-child rows), U = K~_child^{-1} F
+ * (what=1, N x w_l), or the per-node Gram matrices Sw (what=2) / Sx (what=3)
+ * (2^(l-1) blocks of w_l x w_l).  w_out receives w_l.  `count` is the capacity of `out`.  */
+int hodlr_debug_level(hodlr_ctx* h, int what, int level, double* out, int64_t count, int32_t* w_out);
 
 /* Number of K or K_j vector products (columns) of the last build (Sec. 3.2.2 count).  */
 int hodlr_napply(const hodlr_ctx* h, int64_t* out);

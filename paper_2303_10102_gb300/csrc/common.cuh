@@ -31,6 +31,7 @@ struct GemmProfile {
   cudaEvent_t* ev = nullptr;   // 2 per launch
   int cap = 0, n = 0;
   double flops = 0.0, bytes = 0.0;
+  int* shape = nullptr;        // per launch: M, N, K, batch, tA, tB, kernel variant
 };
 extern GemmProfile g_prof;
 inline void count_launch(int n = 1) { g_kernel_launches += n; }

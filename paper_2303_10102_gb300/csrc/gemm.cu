@@ -8,6 +8,7 @@
 #include "ops.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace hodlr {
 
@@ -143,14 +144,20 @@ __global__ void splitk_reduce(GemmArgs g, int nsplit, const Acc* part) {
 
 }  // namespace
 
+bool sgemm_large(const GemmArgs& g, cudaStream_t st);
+
 template <class TA, class TB, class TC, class Acc>
 void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
+                std::is_same<Acc, float>::value) {
+    if (sgemm_large(g, st)) return;
+  }
   int tiles = cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
   int nsplit = 1;
-  if (g.K >= 512 && tiles < 2 * 152) {
-    nsplit = (4 * 152 + tiles - 1) / tiles;
-    nsplit = std::min(nsplit, cdiv(g.K, 256));
+  if (g.K >= 512 && tiles < 4 * 152) {
+    nsplit = (8 * 152 + tiles - 1) / tiles;
+    nsplit = std::min(nsplit, cdiv(g.K, 128));
     size_t per = (size_t)g.batch * g.M * g.N * sizeof(Acc);
     if (per > 0) nsplit = (int)std::min<size_t>(nsplit, s.bytes / per);
     if (nsplit < 2) nsplit = 1;
@@ -169,6 +176,10 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   check_launch("gemm_kernel");
   if (prof) {
     cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = g.M; sh[1] = g.N; sh[2] = g.K; sh[3] = g.batch; sh[4] = g.tA; sh[5] = g.tB; sh[6] = 10 * nsplit;
+    }
     ++g_prof.n;
     double mnk = (double)g.M * g.N * g.K * g.batch;
     g_prof.flops += 2.0 * mnk;
@@ -192,5 +203,294 @@ template void gemm<double, double, float, double>(const GemmArgs&, Scratch, cuda
 template void gemm<float, float, float, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm<double, float, float, float>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm<double, float, double, double>(const GemmArgs&, Scratch, cudaStream_t);
+
+}  // namespace hodlr
+
+// =============================================================================================
+// Double-float GEMM: operands split into (hi, lo) FP32 pairs and products accumulated in
+// double-float (about 48 significant bits) on the FP32 pipes.  GB300's FP64 rate is far below
+// its FP32 rate, so sums that need more than FP32 accuracy (leaf sketches whose row sums are
+// thousands of times the nugget; the Woodbury factorization sweeps) use this path.
+namespace hodlr {
+namespace {
+
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_from(double x) {
+  float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ DF df_from(float x) { return {x, 0.0f}; }
+// acc += a * b (double-float), error-free product of the high parts plus the cross terms
+__device__ __forceinline__ DF df_fma(DF acc, DF a, DF b) {
+  float p = a.hi * b.hi;
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  float s = acc.hi + p;
+  float bb = s - acc.hi;
+  float e = (acc.hi - (s - bb)) + (p - bb);
+  e += acc.lo + pe;
+  float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+
+template <class TA, class TB, class TC>
+__global__ void __launch_bounds__(NT) gemm_df_kernel(GemmArgs g, int nsplit, int kchunk, double* part) {
+  __shared__ DF As[BK][BM + 1];
+  __shared__ DF Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BM / TM);
+  const int ty = tid / (BM / TM);
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int b = blockIdx.z / nsplit, s = blockIdx.z % nsplit;
+  int bi = b;
+  if (g.bmap == BMAP_XOR1) bi = b ^ 1;
+  else if (g.bmap == BMAP_SHR1) bi = b >> 1;
+  long long aoff = (long long)b * g.sA, boff = (long long)bi * g.sB, coff = (long long)b * g.sC;
+  int M = g.M, K = g.K;
+  if (g.offmode == 1) {
+    int r0 = g.off[b];
+    M = g.off[b + 1] - r0; aoff = r0; coff = r0;
+  } else if (g.offmode == 2) {
+    int r0 = g.off[b];
+    K = g.off[b + 1] - r0; aoff = r0; boff = r0;
+  }
+  const int kb = s * kchunk, ke = min(K, kb + kchunk);
+  if (m0 >= M) return;
+  const TA* A = (const TA*)g.A + aoff;
+  const TB* B = (const TB*)g.B + boff;
+  DF acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = {0.0f, 0.0f};
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += NT) {
+      int i, k;
+      if (!g.tA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
+      int gi = m0 + i, gk = k0 + k;
+      DF v = {0.0f, 0.0f};
+      if (gi < M && gk < ke) v = df_from(g.tA ? A[gk + (long long)gi * g.lda] : A[gi + (long long)gk * g.lda]);
+      As[k][i] = v;
+    }
+    for (int e = tid; e < BK * BN; e += NT) {
+      int k, j;
+      if (!g.tB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
+      int gj = n0 + j, gk = k0 + k;
+      DF v = {0.0f, 0.0f};
+      if (gj < g.N && gk < ke) v = df_from(g.tB ? B[gj + (long long)gk * g.ldb] : B[gk + (long long)gj * g.ldb]);
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      DF a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[k][tx + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[k][ty + j * (BN / TN)];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = df_fma(acc[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < TN; ++j) {
+    int gj = n0 + ty + j * (BN / TN);
+    if (gj >= g.N) continue;
+    for (int i = 0; i < TM; ++i) {
+      int gi = m0 + tx + i * (BM / TM);
+      if (gi >= M) continue;
+      double v = (double)acc[i][j].hi + (double)acc[i][j].lo;
+      if (nsplit == 1) {
+        TC* C = (TC*)g.C + coff;
+        long long o = gi + (long long)gj * g.ldc;
+        double r = g.alpha * v;
+        if (g.beta != 0.0) r += g.beta * (double)C[o];
+        C[o] = (TC)r;
+      } else {
+        part[((long long)b * nsplit + s) * (long long)g.M * g.N + gi + (long long)gj * g.M] = v;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <class TA, class TB, class TC>
+void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  int tiles = cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
+  int nsplit = 1;
+  if (g.K >= 512 && tiles < 2 * 152) {
+    nsplit = (4 * 152 + tiles - 1) / tiles;
+    nsplit = std::min(nsplit, cdiv(g.K, 256));
+    size_t per = (size_t)g.batch * g.M * g.N * sizeof(double);
+    if (per > 0) nsplit = (int)std::min<size_t>(nsplit, s.bytes / per);
+    if (nsplit < 2) nsplit = 1;
+  }
+  int kchunk = g.K;
+  if (nsplit > 1) {
+    kchunk = ((cdiv(g.K, nsplit) + BK - 1) / BK) * BK;
+    nsplit = cdiv(g.K, kchunk);
+  }
+  if (g.K <= 0) kchunk = 0;
+  dim3 grid(cdiv(g.M, BM), cdiv(g.N, BN), g.batch * nsplit);
+  if (grid.z > 65535) throw Error(-1, "gemm_df: batch too large");
+  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+  gemm_df_kernel<TA, TB, TC><<<grid, NT, 0, st>>>(g, nsplit, kchunk, (double*)s.ptr);
+  check_launch("gemm_df_kernel");
+  if (prof) {
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = g.M; sh[1] = g.N; sh[2] = g.K; sh[3] = g.batch; sh[4] = g.tA; sh[5] = g.tB; sh[6] = 2;
+    }
+    ++g_prof.n;
+    g_prof.flops += 2.0 * (double)g.M * g.N * g.K * g.batch;
+  }
+  if (nsplit > 1) {
+    long long mn = (long long)g.M * g.N;
+    dim3 rg(cdiv(mn, 256), g.batch);
+    splitk_reduce<TC, double><<<rg, 256, 0, st>>>(g, nsplit, (const double*)s.ptr);
+    check_launch("splitk_reduce");
+  }
+}
+template void gemm_df<double, double, double>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm_df<float, double, double>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm_df<double, float, double>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm_df<float, float, double>(const GemmArgs&, Scratch, cudaStream_t);
+
+}  // namespace hodlr
+
+// =============================================================================================
+// Large-tile FP32 GEMM (128 x 128 tile, 8 x 8 outputs per thread, register-prefetched double
+// buffering in shared memory).  Used for the wide FP32 contractions of the trace sweeps and the
+// Woodbury solves when both M and N are large; everything else goes to the generic kernel.
+namespace hodlr {
+namespace {
+
+constexpr int LBM = 128, LBN = 128, LBK = 8, LNT = 256;
+
+__global__ void __launch_bounds__(LNT, 2) sgemm_large_kernel(GemmArgs g) {
+  __shared__ float As[2][LBK][LBM + 4];
+  __shared__ float Bs[2][LBK][LBN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;          // 16 x 16 threads, 8 x 8 outputs each
+  const int m0 = blockIdx.x * LBM, n0 = blockIdx.y * LBN;
+  const int b = blockIdx.z;
+  int bi = b;
+  if (g.bmap == BMAP_XOR1) bi = b ^ 1;
+  else if (g.bmap == BMAP_SHR1) bi = b >> 1;
+  const float* A = (const float*)g.A + (long long)b * g.sA;
+  const float* B = (const float*)g.B + (long long)bi * g.sB;
+  float* C = (float*)g.C + (long long)b * g.sC;
+  const int M = g.M, N = g.N, K = g.K;
+  // each thread loads 4 elements of the A tile and 4 of the B tile per stage
+  float ra[4], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * LNT;
+      int i, k;
+      if (!g.tA) { i = e % LBM; k = e / LBM; } else { k = e % LBK; i = e / LBK; }
+      int gi = m0 + i, gk = k0 + k;
+      ra[r] = (gi < M && gk < K) ? (g.tA ? A[gk + (long long)gi * g.lda] : A[gi + (long long)gk * g.lda]) : 0.f;
+      int j;
+      if (!g.tB) { k = e % LBK; j = e / LBK; } else { j = e % LBN; k = e / LBN; }
+      int gj = n0 + j;
+      gk = k0 + k;
+      rb[r] = (gj < N && gk < K) ? (g.tB ? B[gj + (long long)gk * g.ldb] : B[gk + (long long)gj * g.ldb]) : 0.f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * LNT;
+      int i, k;
+      if (!g.tA) { i = e % LBM; k = e / LBM; } else { k = e % LBK; i = e / LBK; }
+      As[buf][k][i] = ra[r];
+      int j;
+      if (!g.tB) { k = e % LBK; j = e / LBK; } else { j = e % LBN; k = e / LBN; }
+      Bs[buf][k][j] = rb[r];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  load(0);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += LBK) {
+    const bool more = k0 + LBK < K;
+    if (more) load(k0 + LBK);
+#pragma unroll
+    for (int k = 0; k < LBK; ++k) {
+      float a[8], bb[8];
+      // rows tx*4 .. +3 and 64 + tx*4 .. +3; cols ty*4 .. +3 and 64 + ty*4 .. +3
+      float4 a0 = *(const float4*)&As[buf][k][tx * 4];
+      float4 a1 = *(const float4*)&As[buf][k][64 + tx * 4];
+      float4 b0 = *(const float4*)&Bs[buf][k][ty * 4];
+      float4 b1 = *(const float4*)&Bs[buf][k][64 + ty * 4];
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      bb[0] = b0.x; bb[1] = b0.y; bb[2] = b0.z; bb[3] = b0.w; bb[4] = b1.x; bb[5] = b1.y; bb[6] = b1.z; bb[7] = b1.w;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  const float alpha = (float)g.alpha, beta = (float)g.beta;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int gj = n0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + j - 4);
+    if (gj >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int gi = m0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + i - 4);
+      if (gi >= M) continue;
+      long long o = gi + (long long)gj * g.ldc;
+      float v = alpha * acc[i][j];
+      if (beta != 0.f) v += beta * C[o];
+      C[o] = v;
+    }
+  }
+}
+
+}  // namespace
+
+bool sgemm_large(const GemmArgs& g, cudaStream_t st) {
+  if (g.offmode != 0 || g.M < 256 || g.N < 96 || g.K < 8) return false;
+  dim3 grid(cdiv(g.M, LBM), cdiv(g.N, LBN), g.batch);
+  if (grid.z > 65535) return false;
+  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+  sgemm_large_kernel<<<grid, LNT, 0, st>>>(g);
+  check_launch("sgemm_large_kernel");
+  if (prof) {
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = g.M; sh[1] = g.N; sh[2] = g.K; sh[3] = g.batch; sh[4] = g.tA; sh[5] = g.tB; sh[6] = 1;
+    }
+    ++g_prof.n;
+    g_prof.flops += 2.0 * (double)g.M * g.N * g.K * g.batch;
+    g_prof.bytes += ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N * (g.beta != 0.0 ? 2 : 1)) * 4.0 *
+                    g.batch;
+  }
+  return true;
+}
 
 }  // namespace hodlr

@@ -21,7 +21,10 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -57,6 +60,8 @@ struct Base {
   virtual void solve_nat(const double* b, double* x) = 0;
   virtual void traces(double* t, double* f) = 0;
   virtual void set_pivots(const int32_t* piv) = 0;
+  virtual void logdet_levels(double* out) = 0;
+  virtual void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) = 0;
   virtual void get_pivots(int32_t* piv) const = 0;
   int N = 0, tau = 0, leaf = 0, c = 0, cap = 0, nleaves = 0;
   std::vector<int64_t> perm64;
@@ -80,7 +85,6 @@ struct Engine : Base {
   cudaStream_t st;
   // tree
   std::vector<std::vector<int>> bnd;     // per depth: node boundaries (2^d + 1)
-  int* d_perm = nullptr;                 // tree position -> natural index (var-major chunk layout)
   int* d_perm_plain = nullptr;           // tree position -> natural index (plain)
   std::vector<unsigned char*> d_mask;    // per level (1..tau): right-child rows
   int* d_leafb = nullptr;
@@ -93,14 +97,20 @@ struct Engine : Base {
   // leaves
   T *A = nullptr, *Ainv = nullptr, *dA[2] = {nullptr, nullptr};
   double* leaflog = nullptr;
-  // physics state
-  T *lam0 = nullptr, *lam1 = nullptr, *tw = nullptr, *Sdst = nullptr;
-  double* coef = nullptr;
-  void* fftw = nullptr;
-  size_t fftw_bytes = 0;
-  int qc = 0;                            // physics column chunk
-  T *nx = nullptr, *na = nullptr, *nb_ = nullptr, *nu_ = nullptr, *nu2 = nullptr, *ns = nullptr, *ne = nullptr,
-    *nt = nullptr, *nw = nullptr;
+  // physics state (one set per arithmetic type)
+  template <class V> struct Phys {
+    V *lam0 = nullptr, *lam1 = nullptr, *tw = nullptr, *S = nullptr;
+    void* fftw = nullptr;
+    size_t fftw_bytes = 0;
+    int qc = 0;                            // physics column chunk
+    int* perm = nullptr;                   // tree position -> natural index (var-major chunk layout)
+    V *nx = nullptr, *na = nullptr, *nb = nullptr, *nu = nullptr, *nu2 = nullptr, *ns = nullptr, *ne = nullptr,
+      *nt = nullptr, *nw = nullptr;
+    int df = 0;                            // 2-D DST products with double-float accumulation
+  };
+  Phys<T> P;                               // working precision
+  Phys<double> P64;                        // FP64-class leaf sketch of the mixed path
+  double* coef = nullptr;                  // Thomas tables (shared)
   // sketch buffers
   T *R = nullptr, *KR = nullptr, *KjR[2] = {nullptr, nullptr}, *Y = nullptr, *S = nullptr, *KS = nullptr,
     *KjS[2] = {nullptr, nullptr}, *dS = nullptr, *KdS = nullptr, *YJ = nullptr, *Q1 = nullptr;
@@ -129,7 +139,7 @@ struct Engine : Base {
   Engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t s_) {
     dim = m->dim; G = m->grid[0]; nvar = m->nvar; nu = m->nu; prec = m->precision;
     leaf = o->leaf; cap = o->rank_or_cap; c = o->rank_or_cap + o->oversample; tol = o->tol; seed = o->seed;
-    guard = 1e-5;
+    guard = o->guard > 0.0 ? o->guard : 1e-5;
     st = s_;
     if (dim < 1 || dim > 2 || nvar < 1 || nvar > 2 || G < 2 || leaf < nvar || leaf % nvar || cap < 1 || c < cap ||
         (nu != 0.5 && nu != 1.5))
@@ -209,12 +219,26 @@ struct Engine : Base {
 
   static T* plan_or(T* base, size_t off) { return base ? base + off : nullptr; }
 
+  template <class V> void carve_phys(Arena& ar, Phys<V>& Q, int qc) {
+    qc += qc & 1;
+    Q.qc = qc;
+    size_t nemb = dim == 1 ? ph.L : (size_t)ph.L * ph.L;
+    Q.perm = ar.take<int>(N);
+    Q.lam0 = ar.take<V>(nemb);
+    Q.lam1 = ar.take<V>(nemb);
+    Q.tw = ar.take<V>(2 * (size_t)ph.L + 16);
+    if (dim == 2) Q.S = ar.take<V>((size_t)G * G);
+    Q.fftw_bytes = std::max(fft_work_bytes(ph, qc, sizeof(V)), nemb * (sizeof(V) * 3) + 512);
+    Q.fftw = ar.take<char>(Q.fftw_bytes);
+    size_t nat = (size_t)nvar * Ns * qc;
+    Q.nx = ar.take<V>(nat); Q.na = ar.take<V>(nat); Q.nb = ar.take<V>(nat); Q.nu = ar.take<V>(nat);
+    Q.nu2 = ar.take<V>(nat); Q.ns = ar.take<V>(nat); Q.ne = ar.take<V>(nat); Q.nt = ar.take<V>(nat);
+    Q.nw = ar.take<V>(nat);
+  }
+
   // ---------------------------------------------------------------- workspace plan / carve
   void carve(Arena& ar) {
     const size_t NN = (size_t)N;
-    qc = std::min(64, std::max(c, 2));
-    qc += qc & 1;
-    d_perm = ar.take<int>(N);
     d_perm_plain = ar.take<int>(N);
     d_mask.assign(tau + 1, nullptr);
     for (int l = 1; l <= tau; ++l) d_mask[l] = ar.take<unsigned char>(N);
@@ -240,18 +264,9 @@ struct Engine : Base {
     dA[1] = ar.take<T>(nl2);
     leaflog = ar.take<double>(nleaves);
     // physics
-    size_t nemb = dim == 1 ? ph.L : (size_t)ph.L * ph.L;
-    lam0 = ar.take<T>(nemb);
-    lam1 = ar.take<T>(nemb);
-    tw = ar.take<T>(2 * (size_t)ph.L + 16);
+    carve_phys(ar, P, std::min(64, std::max(c, 2)));
+    if (sizeof(T) == 4) { carve_phys(ar, P64, 16); P64.df = 1; }
     coef = ar.take<double>(dim == 1 ? 2 * (size_t)G : 2 * (size_t)G * G);
-    if (dim == 2) Sdst = ar.take<T>((size_t)G * G);
-    fftw_bytes = std::max(fft_work_bytes(ph, qc, sizeof(T)), nemb * (sizeof(T) * 3) + 512);
-    fftw = ar.take<char>(fftw_bytes);
-    size_t nat = (size_t)nvar * Ns * qc;
-    nx = ar.take<T>(nat); na = ar.take<T>(nat); nb_ = ar.take<T>(nat); nu_ = ar.take<T>(nat);
-    nu2 = ar.take<T>(nat); ns = ar.take<T>(nat); ne = ar.take<T>(nat); nt = ar.take<T>(nat);
-    nw = ar.take<T>(nat);
     // sketch
     R = ar.take<T>(NN * c); KR = ar.take<T>(NN * c); KjR[0] = ar.take<T>(NN * c); KjR[1] = ar.take<T>(NN * c);
     Y = ar.take<T>(NN * c);
@@ -293,7 +308,7 @@ struct Engine : Base {
     vec_d3 = ar.take<double>(NN * 2);
     vec_t = ar.take<T>(NN * 2);
     red = ar.take<double>((size_t)std::max(maxb, nleaves) * 16 + 64);
-    res = ar.take<double>(256);
+    res = ar.take<double>(256 + 64);
     Afp = ar.take<double>(nl2);
     sgbuf = ar.take<double>((size_t)maxb * cap * cap);
     fg64 = ar.take<double>((size_t)maxb * cap * cap);
@@ -305,14 +320,11 @@ struct Engine : Base {
   }
 
   void upload_tree() {
-    std::vector<int> pp(N), pv(N);
-    for (int i = 0; i < N; ++i) {
-      int n = (int)perm64[i];
-      pp[i] = n;
-      pv[i] = nvar == 1 ? n : (n % Ns) + (n / Ns) * (Ns * qc);
-    }
-    HODLR_CUDA(cudaMemcpyAsync(d_perm, pv.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<int> pp(N);
+    for (int i = 0; i < N; ++i) pp[i] = (int)perm64[i];
     HODLR_CUDA(cudaMemcpyAsync(d_perm_plain, pp.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    upload_phys(P);
+    if (P64.perm) upload_phys(P64);
     for (int l = 1; l <= tau; ++l) {
       std::vector<unsigned char> m(N, 0);
       const auto& b = bnd[l];
@@ -322,11 +334,20 @@ struct Engine : Base {
       HODLR_CUDA(cudaStreamSynchronize(st));
     }
     HODLR_CUDA(cudaMemcpyAsync(d_leafb, bnd[tau].data(), (nleaves + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (dim == 2) dst_matrix<T>(G, Sdst, st);
-    if (ph.L1 == 0) twiddles<T>(ph.L, tw, st);
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+  template <class V> void upload_phys(Phys<V>& Q) {
+    std::vector<int> pv(N);
+    for (int i = 0; i < N; ++i) {
+      int n = (int)perm64[i];
+      pv[i] = nvar == 1 ? n : (n % Ns) + (n / Ns) * (Ns * Q.qc);
+    }
+    HODLR_CUDA(cudaMemcpyAsync(Q.perm, pv.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (dim == 2) dst_matrix<V>(G, Q.S, st);
+    if (ph.L1 == 0) twiddles<V>(ph.L, Q.tw, st);
     else {
-      twiddles<T>(ph.L1, tw, st);
-      twiddles<T>(ph.L2, tw + (ph.L1 / 2) * 2, st);
+      twiddles<V>(ph.L1, Q.tw, st);
+      twiddles<V>(ph.L2, Q.tw + (ph.L1 / 2) * 2, st);
     }
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
@@ -358,31 +379,48 @@ struct Engine : Base {
 
   // out -= sum over levels in [l0, l1] of H_l X (or dH^(j)_l X) ; X, out: N x q row panels
   void offdiag(int l0, int l1, int j, const T* X, long long ldx, int q, T* out, long long ldo, double sign = -1.0) {
+    offdiag_t<T>(l0, l1, j, X, ldx, q, out, ldo, sign);
+  }
+  // GEMM with a factor panel (type T) and V panels: V == T in working precision, V = double with
+  // double-float accumulation in the mixed path
+  template <class V> void fgemm(const GemmArgs& g) {
+    if constexpr (std::is_same<V, T>::value) gemm<T, T, T, T>(g, scratch, st);
+    else gemm_df<T, V, V>(g, scratch, st);
+  }
+  template <class V>
+  void offdiag_t(int l0, int l1, int j, const V* X, long long ldx, int q, V* out, long long ldo, double sign = -1.0) {
     for (int l = l0; l <= l1; ++l) {
       int wl = w[l];
       if (wl == 0 || q == 0) continue;
       int m = msize(l);
       int nbk = 1 << l;
-      const T* Fl = F[l];
-      // T1_b = F[b]^T X[b]   (wl x q per child block, ld wl)
-      block_tn(l, wl, q, Fl, X, ldx, tpan, wl, (long long)wl * q);
-      GemmArgs g;
-      g.M = m; g.N = q; g.K = wl;
-      g.lda = N; g.sA = m;
-      g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
-      g.C = out; g.ldc = ldo; g.sC = m;
-      g.alpha = sign; g.beta = 1.0; g.batch = nbk;
+      V* tp = (V*)tpan;
+      V* tp2 = tp + (size_t)nbk * wl * q;
+      auto tn = [&](const T* Fp, V* C) {   // C_b = F[b]^T X[b]  (wl x q per child block)
+        GemmArgs g;
+        g.M = wl; g.N = q; g.K = m;
+        g.A = Fp; g.lda = N; g.sA = m; g.tA = 1;
+        g.B = X; g.ldb = ldx; g.sB = m;
+        g.C = C; g.ldc = wl; g.sC = (long long)wl * q; g.batch = nbk;
+        fgemm<V>(g);
+      };
+      auto nn = [&](const T* Fp, const V* Bp) {   // out[b] += sign F[b] C_{b^1}
+        GemmArgs g;
+        g.M = m; g.N = q; g.K = wl;
+        g.A = Fp; g.lda = N; g.sA = m;
+        g.B = Bp; g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
+        g.C = out; g.ldc = ldo; g.sC = m;
+        g.alpha = sign; g.beta = 1.0; g.batch = nbk;
+        fgemm<V>(g);
+      };
       if (j < 0) {
-        g.A = Fl; g.B = tpan;
-        gemmT(g);
+        tn(F[l], tp);
+        nn(F[l], tp);
       } else {
-        const T* dFl = dF[j][l];
-        T* t2p = tpan + (size_t)nbk * wl * q;
-        block_tn(l, wl, q, dFl, X, ldx, t2p, wl, (long long)wl * q);
-        g.A = dFl; g.B = tpan;          // dQ (B~^T x2) and dB~ (Q^T x1)
-        gemmT(g);
-        g.A = Fl; g.B = t2p;            // Q (dB~^T x2) and B~ (dQ^T x1)
-        gemmT(g);
+        tn(F[l], tp);
+        tn(dF[j][l], tp2);
+        nn(dF[j][l], tp);   // dQ (B~^T x2) and dB~ (Q^T x1)
+        nn(F[l], tp2);      // Q (dB~^T x2) and B~ (dQ^T x1)
       }
     }
   }
@@ -390,79 +428,85 @@ struct Engine : Base {
   // ---------------------------------------------------------------- physics product
   const double* th = theta_built;
   void set_physics(const double* theta) {
-    matern_spectra<T>(ph, theta[0], theta[1], lam0, lam1, fftw, tw, st);
+    matern_spectra<T>(ph, theta[0], theta[1], P.lam0, P.lam1, P.fftw, P.tw, st);
+    if (P64.perm) matern_spectra<double>(ph, theta[0], theta[1], P64.lam0, P64.lam1, P64.fftw, P64.tw, st);
     tridiag_tables(ph, theta[2], coef, st);
   }
-  void Ainv_nat(const T* in, T* out, int q) {
-    solve_A<T>(ph, q, in, Ns, out, Ns, coef, Sdst, nw, scratch, st);
+  template <class V> void Ainv_nat(Phys<V>& Q, const V* in, V* out, int q) {
+    solve_A<V>(ph, q, in, Ns, out, Ns, coef, Q.S, Q.nw, scratch, st, Q.df);
   }
   // K X, K_ell X, K_kappa X on a tree-order panel (q columns); any output may be null
   void apply(const T* X, long long ldx, int q, T* oK, T* oL, T* oKap, long long ldo) {
-    const double s2 = th[0], kap = th[2], t2 = th[3];
-    (void)s2;
+    apply_t<T>(P, X, ldx, q, oK, oL, oKap, ldo);
+  }
+  template <class V>
+  void apply_t(Phys<V>& Q, const V* X, long long ldx, int q, V* oK, V* oL, V* oKap, long long ldo) {
+    const double kap = th[2], t2 = th[3];
+    const int qc = Q.qc;
     const size_t vs = (size_t)Ns * qc;   // variable stride in natural buffers
     for (int c0 = 0; c0 < q; c0 += qc) {
       int qq = std::min(qc, q - c0);
-      const T* Xc = X + (size_t)c0 * ldx;
-      permute_rows<T, T>(Xc, ldx, nx, Ns, d_perm, N, qq, 1, st);
-      auto out = [&](T* dst, const T* src) {
-        if (dst) permute_rows<T, T>(src, Ns, dst + (size_t)c0 * ldo, ldo, d_perm, N, qq, 0, st);
+      const V* Xc = X + (size_t)c0 * ldx;
+      permute_rows<V, V>(Xc, ldx, Q.nx, Ns, Q.perm, N, qq, 1, st);
+      auto out = [&](V* dst, const V* src) {
+        if (dst) permute_rows<V, V>(src, Ns, dst + (size_t)c0 * ldo, ldo, Q.perm, N, qq, 0, st);
       };
       if (nvar == 1) {
-        Ainv_nat(nx, na, qq);                                              // a = A^{-1} x
-        if (oKap) Ainv_nat(na, nb_, qq);                                   // b = A^{-2} x
-        if (oK || oKap || oL) fft_convolve<T>(ph, qq, na, Ns, lam0, oL ? lam1 : nullptr, nu_, nu2, Ns, fftw, tw, st);
-        if (oKap) fft_convolve<T>(ph, qq, nb_, Ns, lam0, nullptr, ns, nullptr, Ns, fftw, tw, st);
-        if (oK || oKap) Ainv_nat(nu_, ne, qq);                             // e = A^{-1} K_u a
+        Ainv_nat(Q, Q.nx, Q.na, qq);                                        // a = A^{-1} x
+        if (oKap) Ainv_nat(Q, Q.na, Q.nb, qq);                              // b = A^{-2} x
+        if (oK || oKap || oL)
+          fft_convolve<V>(ph, qq, Q.na, Ns, Q.lam0, oL ? Q.lam1 : nullptr, Q.nu, Q.nu2, Ns, Q.fftw, Q.tw, st);
+        if (oKap) fft_convolve<V>(ph, qq, Q.nb, Ns, Q.lam0, nullptr, Q.ns, nullptr, Ns, Q.fftw, Q.tw, st);
+        if (oK || oKap) Ainv_nat(Q, Q.nu, Q.ne, qq);                        // e = A^{-1} K_u a
         if (oK) {
-          out(oK, ne);
-          axpby<T>(N, qq, t2, Xc, ldx, 1.0, oK + (size_t)c0 * ldo, ldo, st);
+          out(oK, Q.ne);
+          axpby<V>(N, qq, t2, Xc, ldx, 1.0, oK + (size_t)c0 * ldo, ldo, st);
         }
         if (oL) {
-          Ainv_nat(nu2, nt, qq);
-          out(oL, nt);
+          Ainv_nat(Q, Q.nu2, Q.nt, qq);
+          out(oL, Q.nt);
         }
         if (oKap) {
-          axpby<T>(Ns, qq, 1.0, ns, Ns, 1.0, ne, Ns, st);                  // e + K_u b
-          Ainv_nat(ne, nt, qq);
-          axpby<T>(Ns, qq, 0.0, nt, Ns, -2.0 * kap, nt, Ns, st);
-          out(oKap, nt);
+          axpby<V>(Ns, qq, 1.0, Q.ns, Ns, 1.0, Q.ne, Ns, st);               // e + K_u b
+          Ainv_nat(Q, Q.ne, Q.nt, qq);
+          axpby<V>(Ns, qq, 0.0, Q.nt, Ns, -2.0 * kap, Q.nt, Ns, st);
+          out(oKap, Q.nt);
         }
-        napply += (long long)qq * ((oK ? 1 : 0) + (oL ? 1 : 0) + (oKap ? 1 : 0));
       } else {
-        T* x1 = nx;
-        T* x2 = nx + vs;
-        T* a = na;
-        T* wv = na + vs;
-        Ainv_nat(x2, a, qq);                                               // a = A^{-1} x2
-        axpby<T>(Ns, qq, 1.0, x1, Ns, 0.0, wv, Ns, st);
-        axpby<T>(Ns, qq, 1.0, a, Ns, 1.0, wv, Ns, st);                     // w = x1 + a  (L^T x)
-        T* u = nu_;        // [u; c1]
-        T* u2 = nu2;       // [u'; c2]
-        T* s = ns;         // [s; c3]
-        if (oK || oKap || oL) fft_convolve<T>(ph, qq, wv, Ns, lam0, oL ? lam1 : nullptr, u, u2, Ns, fftw, tw, st);
-        if (oK || oKap) Ainv_nat(u, u + vs, qq);                           // c1 = A^{-1} u
+        V* x1 = Q.nx;
+        V* x2 = Q.nx + vs;
+        V* a = Q.na;
+        V* wv = Q.na + vs;
+        Ainv_nat(Q, x2, a, qq);                                             // a = A^{-1} x2
+        axpby<V>(Ns, qq, 1.0, x1, Ns, 0.0, wv, Ns, st);
+        axpby<V>(Ns, qq, 1.0, a, Ns, 1.0, wv, Ns, st);                      // w = x1 + a  (L^T x)
+        V* u = Q.nu;       // [u; c1]
+        V* u2 = Q.nu2;     // [u'; c2]
+        V* s = Q.ns;       // [s; c3]
+        if (oK || oKap || oL)
+          fft_convolve<V>(ph, qq, wv, Ns, Q.lam0, oL ? Q.lam1 : nullptr, u, u2, Ns, Q.fftw, Q.tw, st);
+        if (oK || oKap) Ainv_nat(Q, u, u + vs, qq);                         // c1 = A^{-1} u
         if (oK) {
           out(oK, u);
-          axpby<T>(N, qq, t2, Xc, ldx, 1.0, oK + (size_t)c0 * ldo, ldo, st);
+          axpby<V>(N, qq, t2, Xc, ldx, 1.0, oK + (size_t)c0 * ldo, ldo, st);
         }
         if (oL) {
-          Ainv_nat(u2, u2 + vs, qq);
+          Ainv_nat(Q, u2, u2 + vs, qq);
           out(oL, u2);
         }
         if (oKap) {
-          T* b = nb_;
-          Ainv_nat(a, b, qq);                                              // b = A^{-2} x2
-          fft_convolve<T>(ph, qq, b, Ns, lam0, nullptr, s, nullptr, Ns, fftw, tw, st);   // s = K_u b
-          axpby<T>(Ns, qq, 1.0, u + vs, Ns, 0.0, nt, Ns, st);
-          axpby<T>(Ns, qq, 1.0, s, Ns, 1.0, nt, Ns, st);                   // c1 + s
-          Ainv_nat(nt, s + vs, qq);                                        // c3
-          axpby<T>(Ns, qq, 0.0, s, Ns, -2.0 * kap, s, Ns, st);             // -2 kappa [s; c3]
-          axpby<T>(Ns, qq, 0.0, s + vs, Ns, -2.0 * kap, s + vs, Ns, st);
+          V* b = Q.nb;
+          Ainv_nat(Q, a, b, qq);                                            // b = A^{-2} x2
+          fft_convolve<V>(ph, qq, b, Ns, Q.lam0, nullptr, s, nullptr, Ns, Q.fftw, Q.tw, st);   // s = K_u b
+          axpby<V>(Ns, qq, 1.0, u + vs, Ns, 0.0, Q.nt, Ns, st);
+          axpby<V>(Ns, qq, 1.0, s, Ns, 1.0, Q.nt, Ns, st);                  // c1 + s
+          Ainv_nat(Q, Q.nt, s + vs, qq);                                    // c3
+          axpby<V>(Ns, qq, 0.0, s, Ns, -2.0 * kap, s, Ns, st);              // -2 kappa [s; c3]
+          axpby<V>(Ns, qq, 0.0, s + vs, Ns, -2.0 * kap, s + vs, Ns, st);
           out(oKap, s);
         }
-        napply += (long long)qq * ((oK ? 1 : 0) + (oL ? 1 : 0) + (oKap ? 1 : 0));
       }
+      napply += (long long)qq * ((oK ? 1 : 0) + (oL ? 1 : 0) + (oKap ? 1 : 0));
     }
   }
 
@@ -599,27 +643,34 @@ struct Engine : Base {
     g.C = Cp; g.ldc = n; g.sC = (long long)n * n; g.batch = nb;
     gemmT(g);
   }
-  // copy the right-child rows of src (N x wl) into dst
+  // copy the right-child rows of src (N x wl) into dst, keeping only the first rank_p columns of
+  // pair p (B~ = Z[c2, :r]): the shared sketch panel carries other pairs' columns beyond r_p
   void copy_rows_c2(int l, int wl, const T* src, T* dst) {
     int m = msize(l);
     copy_blocks<T, T>(npairs(l), m, wl, src + m, N, 2LL * m, dst + m, N, 2LL * m, 1.0, st);
+    zero_pad_cols(l, wl, dst + m);
   }
+  void zero_pad_cols(int l, int wl, T* rows);
 
   // ---------------------------------------------------------------- leaves (eq. leaf sample, eq. diag diff)
   void build_leaves() {
     const int nl = leaf;
-    // S_leaf = stacked identities
-    T* Sl = WP;  // N x nl
-    fill<T>(Sl, T(0), (long long)N * nl, st);
-    identity_blocks(Sl);
-    apply(Sl, N, nl, E[0], E[1], E[2], N);
-    offdiag(1, tau, -1, Sl, N, nl, E[0], N);
-    offdiag(1, tau, 0, Sl, N, nl, E[1], N);
-    offdiag(1, tau, 1, Sl, N, nl, E[2], N);
-    extract_leaves<T, double>(nleaves, nl, d_leafb, E[0], N, Afp, st);
+    if (sizeof(T) == 4) {
+      build_leaves_hp();
+    } else {
+      // S_leaf = stacked identities
+      T* Sl = WP;  // N x nl
+      fill<T>(Sl, T(0), (long long)N * nl, st);
+      identity_blocks(Sl);
+      apply(Sl, N, nl, E[0], E[1], E[2], N);
+      offdiag(1, tau, -1, Sl, N, nl, E[0], N);
+      offdiag(1, tau, 0, Sl, N, nl, E[1], N);
+      offdiag(1, tau, 1, Sl, N, nl, E[2], N);
+      extract_leaves<T, double>(nleaves, nl, d_leafb, E[0], N, Afp, st);
+      extract_leaves<T, T>(nleaves, nl, d_leafb, E[1], N, dA[0], st);
+      extract_leaves<T, T>(nleaves, nl, d_leafb, E[2], N, dA[1], st);
+    }
     convert<double, T>(Afp, A, (long long)nleaves * nl * nl, st);
-    extract_leaves<T, T>(nleaves, nl, d_leafb, E[1], N, dA[0], st);
-    extract_leaves<T, T>(nleaves, nl, d_leafb, E[2], N, dA[1], st);
     // FP64 leaf Cholesky, log-det and inverse
     potrf_lower(nleaves, nl, Afp, nl, (long long)nl * nl, nullptr, leaflog, d_status, st);
     double* Linv = LinvLeaf;
@@ -634,6 +685,34 @@ struct Engine : Base {
     }
     status_check("leaf Cholesky");
   }
+  // Leaf sketch of the mixed path at FP64-class accuracy: the stacked-identity probe makes each
+  // leaf entry a difference of two row sums over all leaves (eq. leaf sample), whose FP32
+  // rounding would exceed the nugget; the products run in FP64 (FFT, Thomas recurrences, DST
+  // with double-float accumulation) and the peeling in double-float, in column chunks.
+  void build_leaves_hp() {
+    const int nl = leaf;
+    const int qcl = std::max(1, std::min(64, wide / 8));
+    double* Sx = (double*)WP;
+    double* Eh[3] = {Sx + (size_t)N * qcl, Sx + 2 * (size_t)N * qcl, Sx + 3 * (size_t)N * qcl};
+    for (int j0 = 0; j0 < nl; j0 += qcl) {
+      int qq = std::min(qcl, nl - j0);
+      fill<double>(Sx, 0.0, (long long)N * qq, st);
+      identity_cols(Sx, j0, qq);
+      apply_t<double>(P64, Sx, N, qq, Eh[0], Eh[1], Eh[2], N);
+      offdiag_t<double>(1, tau, -1, Sx, N, qq, Eh[0], N);
+      offdiag_t<double>(1, tau, 0, Sx, N, qq, Eh[1], N);
+      offdiag_t<double>(1, tau, 1, Sx, N, qq, Eh[2], N);
+      scatter_leaf_cols<double, double>(Eh[0], j0, qq, Afp);
+      scatter_leaf_cols<double, T>(Eh[1], j0, qq, dA[0]);
+      scatter_leaf_cols<double, T>(Eh[2], j0, qq, dA[1]);
+    }
+    symmetrize_blocks<double>(Afp);
+    symmetrize_blocks<T>(dA[0]);
+    symmetrize_blocks<T>(dA[1]);
+  }
+  void identity_cols(double* Sx, int j0, int qq);
+  template <class TS, class TD> void scatter_leaf_cols(const TS* E, int j0, int qq, TD* Ablk);
+  template <class V> void symmetrize_blocks(V* Ablk);
   void identity_blocks(T* Sl);
 
   // ---------------------------------------------------------------- factorization (App. C)
@@ -679,6 +758,13 @@ struct Engine : Base {
     }
   }
 
+  // FP64-accurate contraction with FP64 output: plain FP64 (DFMA) on the FP64 path, double-float
+  // accumulation on the FP32 pipes on the mixed path (GB300's FP64 rate is low).
+  template <class TA, class TB> void g64(const GemmArgs& g) {
+    if constexpr (sizeof(T) == 8) gemm<TA, TB, double, double>(g, scratch, st);
+    else gemm_df<TA, TB, double>(g, scratch, st);
+  }
+
   // FP64 solve with the depth-d subtrees (factorization sweeps and K~^{-1} y): leaf Cholesky
   // solves and Woodbury corrections in FP64 against the stored factors F (App. C).
   void solve64(const double* in, long long ldi, double* out, long long ldo, int q, int d) {
@@ -692,20 +778,20 @@ struct Engine : Base {
       g.A = out; g.lda = ldo; g.sA = m; g.tA = 1;
       g.B = F[l]; g.ldb = N; g.sB = m;
       g.C = fg64; g.ldc = q; g.sC = (long long)q * wl; g.batch = nbk;
-      gemm<double, T, double, double>(g, scratch, st);
+      g64<double, T>(g);
       GemmArgs h;
       h.M = q; h.N = 2 * wl; h.K = 2 * wl;
       h.A = fg64; h.lda = q; h.sA = 2LL * q * wl;
       h.B = CP64[l]; h.ldb = 2 * wl; h.sB = 4LL * wl * wl; h.tB = 1;
       h.C = stb64; h.ldc = q; h.sC = 2LL * q * wl; h.batch = np;
-      gemm<double, double, double, double>(h, scratch, st);
+      g64<double, double>(h);
       GemmArgs k;
       k.M = m; k.N = q; k.K = wl;
       k.A = U[l]; k.lda = N; k.sA = m;
       k.B = stb64; k.ldb = q; k.sB = (long long)q * wl; k.tB = 1;
       k.C = out; k.ldc = ldo; k.sC = m;
       k.alpha = -1.0; k.beta = 1.0; k.batch = nbk;
-      gemm<double, double, double, double>(k, scratch, st);
+      g64<double, double>(k);
     }
   }
 
@@ -728,7 +814,7 @@ struct Engine : Base {
         g.A = F[l]; g.lda = N; g.sA = m; g.tA = 1;
         g.B = U[l]; g.ldb = N; g.sB = m;
         g.C = sg; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = 1 << l;
-        gemm<T, double, double, double>(g, scratch, st);
+        g64<T, double>(g);
       }
       const long long w2 = (long long)wl * wl;
       // split into Sw (even blocks) and Sx (odd blocks)
@@ -776,7 +862,7 @@ struct Engine : Base {
     g.B = b; g.ldb = n; g.sB = (long long)n * n; g.tB = tb;
     g.C = cc; g.ldc = n; g.sC = (long long)n * n;
     g.alpha = alpha; g.beta = beta; g.batch = nb;
-    gemm<double, double, double, double>(g, scratch, st);
+    g64<double, double>(g);
   }
 
   // ---------------------------------------------------------------- HODLR products (mixed vector type V)
@@ -791,7 +877,7 @@ struct Engine : Base {
       g.A = Lf; g.lda = nl; g.sA = (long long)nl * nl;
       g.B = X; g.ldb = ldx; g.sB = nl;
       g.C = out; g.ldc = ldo; g.sC = nl; g.batch = nleaves;
-      gemm<T, V, V, double>(g, scratch, st);
+      gemm<T, V, V, V>(g, scratch, st);
     }
     for (int l = d + 1; l <= tau; ++l) {
       int wl = w[l];
@@ -804,7 +890,7 @@ struct Engine : Base {
         g.A = Fp; g.lda = N; g.sA = m; g.tA = 1;
         g.B = X; g.ldb = ldx; g.sB = m;
         g.C = C; g.ldc = wl; g.sC = (long long)wl * q; g.batch = nbk;
-        gemm<T, V, V, double>(g, scratch, st);
+        gemm<T, V, V, V>(g, scratch, st);
       };
       auto nn = [&](const T* Fp, const V* Bp) {
         GemmArgs g;
@@ -813,7 +899,7 @@ struct Engine : Base {
         g.B = Bp; g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
         g.C = out; g.ldc = ldo; g.sC = m;
         g.beta = 1.0; g.batch = nbk;
-        gemm<T, V, V, double>(g, scratch, st);
+        gemm<T, V, V, V>(g, scratch, st);
       };
       if (j < 0) {
         tn(F[l], tp);
@@ -1086,6 +1172,41 @@ struct Engine : Base {
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
   void set_unit(double* col, int c0, int qq);
+  void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) override {
+    if (!built || level < 1 || level > tau) throw Error(HODLR_EINVAL, "level");
+    int wl = w[level];
+    *w_out = wl;
+    size_t n = (what <= 1) ? (size_t)N * wl : (size_t)npairs(level) * wl * wl;
+    if ((int64_t)n > count) throw Error(HODLR_EINVAL, "count");
+    double* tmp = vec_d2;
+    if (what == 0) {
+      convert<T, double>(F[level], (double*)WZ, (long long)n, st);
+      HODLR_CUDA(cudaMemcpyAsync(out, WZ, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    } else if (what == 1) {
+      HODLR_CUDA(cudaMemcpyAsync(out, U[level], n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    } else {
+      // recompute the child Grams of this level from F and U (as factor() does)
+      GemmArgs g;
+      int m = msize(level);
+      g.M = wl; g.N = wl; g.K = m;
+      g.A = F[level]; g.lda = N; g.sA = m; g.tA = 1;
+      g.B = U[level]; g.ldb = N; g.sB = m;
+      g.C = sgbuf; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = 1 << level;
+      g64<T, double>(g);
+      const long long w2 = (long long)wl * wl;
+      copy_blocks<double, double>(npairs(level), wl, wl, sgbuf + (what == 3 ? w2 : 0), wl, 2 * w2, sw, wl, w2, 1.0, st);
+      HODLR_CUDA(cudaMemcpyAsync(out, sw, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    (void)tmp;
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+  void logdet_levels(double* out) override {
+    if (!built) throw Error(HODLR_EINVAL, "no build");
+    sum_doubles(leaflog, nleaves, res + 60, 0, st);
+    for (int l = 1; l <= tau; ++l) sum_doubles(d_nodelog[l], npairs(l), res + 60 + l, 0, st);
+    HODLR_CUDA(cudaMemcpyAsync(out, res + 60, sizeof(double) * (tau + 1), cudaMemcpyDeviceToHost, st));
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
   void solve_nat(const double* b, double* x) override {
     if (!built) throw Error(HODLR_EINVAL, "no build");
     permute_rows<double, double>(b, N, vec_d, N, d_perm_plain, N, 1, 0, st);
@@ -1121,6 +1242,48 @@ __global__ void identity_blocks_kernel(const int* bounds, int nl, T* S, long lon
   int lo = bounds[b], n = bounds[b + 1] - lo;
   for (int i = threadIdx.x; i < n; i += blockDim.x) S[lo + i + (size_t)i * ld] = T(1);
 }
+// rows [p*stride, p*stride + m) of pair p: columns j >= rank[p] set to zero
+template <class T>
+__global__ void zero_pad_cols_kernel(int m, long long stride, int wl, const int* rank, T* rows, long long ld) {
+  int p = blockIdx.y;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)m * wl) return;
+  int i = (int)(e % m), j = (int)(e / m);
+  if (j >= rank[p]) rows[p * stride + i + (size_t)j * ld] = T(0);
+}
+__global__ void identity_cols_kernel(const int* bounds, double* S, long long ld, int j0, int qq) {
+  int b = blockIdx.x;
+  int lo = bounds[b], n = bounds[b + 1] - lo;
+  for (int jj = threadIdx.x; jj < qq; jj += blockDim.x)
+    if (j0 + jj < n) S[lo + j0 + jj + (size_t)jj * ld] = 1.0;
+}
+template <class TS, class TD>
+__global__ void scatter_leaf_cols_kernel(const int* bounds, int nl, const TS* E, long long lde, int j0, int qq,
+                                         TD* Ablk) {
+  int b = blockIdx.y;
+  int lo = bounds[b], n = bounds[b + 1] - lo;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)nl * qq) return;
+  int i = (int)(e % nl), jj = (int)(e / nl);
+  int j = j0 + jj;
+  double v = 0.0;
+  if (i < n && j < n) v = (double)E[lo + i + (size_t)jj * lde];
+  else if (i == j) v = 1.0;
+  Ablk[(size_t)b * nl * nl + i + (size_t)j * nl] = (TD)v;
+}
+template <class V>
+__global__ void symmetrize_blocks_kernel(int nl, V* Ablk) {
+  int b = blockIdx.y;
+  V* Ab = Ablk + (size_t)b * nl * nl;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)nl * nl) return;
+  int i = (int)(e % nl), j = (int)(e / nl);
+  if (i <= j) return;
+  V a = Ab[i + (size_t)j * nl], c = Ab[j + (size_t)i * nl];
+  V v = (V)(0.5 * ((double)a + (double)c));
+  Ab[i + (size_t)j * nl] = v;
+  Ab[j + (size_t)i * nl] = v;
+}
 __global__ void unit_cols_kernel(double* col, long long N, int c0, int qq) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < qq) col[c0 + j + (size_t)j * N] = 1.0;
@@ -1144,6 +1307,26 @@ __global__ void scale_sum_kernel(const double* x, int n, double* out, double sca
 template <class T> void Engine<T>::identity_blocks(T* Sl) {
   identity_blocks_kernel<T><<<nleaves, 256, 0, st>>>(d_leafb, leaf, Sl, N);
   check_launch("identity_blocks");
+}
+template <class T> void Engine<T>::zero_pad_cols(int l, int wl, T* rows) {
+  int m = msize(l);
+  dim3 g(cdiv((long long)m * wl, 256), npairs(l));
+  zero_pad_cols_kernel<T><<<g, 256, 0, st>>>(m, 2LL * m, wl, d_rank[l], rows, N);
+  check_launch("zero_pad_cols");
+}
+template <class T> void Engine<T>::identity_cols(double* Sx, int j0, int qq) {
+  identity_cols_kernel<<<nleaves, 64, 0, st>>>(d_leafb, Sx, N, j0, qq);
+  check_launch("identity_cols");
+}
+template <class T> template <class TS, class TD> void Engine<T>::scatter_leaf_cols(const TS* E, int j0, int qq, TD* Ablk) {
+  dim3 g(cdiv((long long)leaf * qq, 256), nleaves);
+  scatter_leaf_cols_kernel<TS, TD><<<g, 256, 0, st>>>(d_leafb, leaf, E, N, j0, qq, Ablk);
+  check_launch("scatter_leaf_cols");
+}
+template <class T> template <class V> void Engine<T>::symmetrize_blocks(V* Ablk) {
+  dim3 g(cdiv((long long)leaf * leaf, 256), nleaves);
+  symmetrize_blocks_kernel<V><<<g, 256, 0, st>>>(leaf, Ablk);
+  check_launch("symmetrize_blocks");
 }
 template <class T> void Engine<T>::set_unit(double* col, int c0, int qq) {
   unit_cols_kernel<<<cdiv(qq, 64), 64, 0, st>>>(col, N, c0, qq);
@@ -1337,6 +1520,14 @@ int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out) {
   if (!t_out || !f_out) return HODLR_EINVAL;
   return guarded(h, [&] { h->e->traces(t_out, f_out); });
 }
+int hodlr_debug_level(hodlr_ctx* h, int what, int level, double* out, int64_t count, int32_t* w_out) {
+  if (!out || !w_out || what < 0 || what > 3) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->debug_level(what, level, out, count, w_out); });
+}
+int hodlr_logdet_levels(hodlr_ctx* h, double* out) {
+  if (!out) return HODLR_EINVAL;
+  return guarded(h, [&] { h->e->logdet_levels(out); });
+}
 int hodlr_napply(const hodlr_ctx* h, int64_t* out) {
   if (!h || !h->e || !out) return HODLR_EINVAL;
   *out = h->e->napply;
@@ -1348,6 +1539,7 @@ int hodlr_profile(hodlr_ctx* h, int enable) {
     if (!g_prof.ev) {
       g_prof.cap = 65536;
       g_prof.ev = new cudaEvent_t[2 * g_prof.cap];
+      g_prof.shape = new int[7 * g_prof.cap];
       for (int i = 0; i < 2 * g_prof.cap; ++i) HODLR_CUDA(cudaEventCreate(&g_prof.ev[i]));
     }
     g_prof.n = 0;
@@ -1371,6 +1563,19 @@ int hodlr_profile_read(hodlr_ctx* h, double* out) {
     }
     out[0] = ms;
     out[1] = g_prof.n;
+    // optional per-launch dump (shape and time) for kernel studies
+    if (const char* path = getenv("HODLR_PROFILE_DUMP")) {
+      if (FILE* f = fopen(path, "w")) {
+        fprintf(f, "M,N,K,batch,tA,tB,variant,ms\n");
+        for (int i = 0; i < g_prof.n; ++i) {
+          float t = 0.f;
+          cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]);
+          const int* sh = g_prof.shape + 7 * i;
+          fprintf(f, "%d,%d,%d,%d,%d,%d,%d,%.6f\n", sh[0], sh[1], sh[2], sh[3], sh[4], sh[5], sh[6], t);
+        }
+        fclose(f);
+      }
+    }
     out[2] = g_prof.flops;
     out[3] = g_prof.bytes;
   } catch (const Error& x) {

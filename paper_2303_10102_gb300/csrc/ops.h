@@ -32,6 +32,9 @@ struct GemmArgs {
 };
 template <class TA, class TB, class TC, class Acc>
 void gemm(const GemmArgs& g, Scratch s, cudaStream_t st);
+// Same contraction with double-float (hi+lo FP32) accumulation on the FP32 pipes (~48 bits).
+template <class TA, class TB, class TC>
+void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st);
 
 // ------------------------------------------------------------------------------ elementwise / data movement
 template <class TS, class TD> void convert(const TS* src, TD* dst, long long n, cudaStream_t st);
@@ -133,7 +136,7 @@ size_t fft_work_bytes(const PhysicsDesc& p, int ncols, int real_bytes);
 // matrix (2-D, G x G); work: Ns*ncols T (2-D).
 template <class T>
 void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out, long long ldo,
-             const double* coef, const T* S, T* work, Scratch s, cudaStream_t st);
+             const double* coef, const T* S, T* work, Scratch s, cudaStream_t st, int df = 0);
 // per-theta coefficient tables of the Thomas recurrences (see physics.cu)
 void tridiag_tables(const PhysicsDesc& p, double kappa, double* coef, cudaStream_t st);
 template <class T> void dst_matrix(int G, T* S, cudaStream_t st);

@@ -754,7 +754,7 @@ template void dst_matrix<float>(int, float*, cudaStream_t);
 
 template <class T>
 void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out, long long ldo, const double* coef,
-             const T* S, T* work, Scratch s, cudaStream_t st) {
+             const T* S, T* work, Scratch s, cudaStream_t st, int df) {
   if (ncols <= 0) return;
   const double scale = p.h * p.h;
   if (p.dim == 1) {
@@ -772,15 +772,21 @@ void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out
   g.A = S; g.lda = G;
   g.B = in; g.ldb = G;
   g.C = work; g.ldc = G;
-  gemm<T, T, T, T>(g, s, st);
+  auto dst = [&](const GemmArgs& a) {
+    if constexpr (sizeof(T) == 8) {
+      if (df) { gemm_df<T, T, T>(a, s, st); return; }
+    }
+    gemm<T, T, T, T>(a, s, st);
+  };
+  dst(g);
   thomas_y_kernel<T><<<cdiv((long long)G * ncols, 128), 128, 0, st>>>(G, ncols, work, Ns, coef, scale);
   check_launch("thomas_y");
   g.B = work; g.C = out;
-  gemm<T, T, T, T>(g, s, st);
+  dst(g);
 }
 template void solve_A<double>(const PhysicsDesc&, int, const double*, long long, double*, long long, const double*,
-                              const double*, double*, Scratch, cudaStream_t);
+                              const double*, double*, Scratch, cudaStream_t, int);
 template void solve_A<float>(const PhysicsDesc&, int, const float*, long long, float*, long long, const double*,
-                             const float*, float*, Scratch, cudaStream_t);
+                             const float*, float*, Scratch, cudaStream_t, int);
 
 }  // namespace hodlr

@@ -35,7 +35,7 @@ class Model(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("leaf", C.c_int), ("rank_or_cap", C.c_int), ("oversample", C.c_int), ("tol", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("guard", C.c_double)]
 
 
 _P = C.c_void_p
@@ -60,6 +60,8 @@ SIGNATURES = {
     "hodlr_solve": (C.c_int, [_P, _P, _P]),
     "hodlr_logdet": (C.c_int, [_P, _D]),
     "hodlr_traces": (C.c_int, [_P, _D, _D]),
+    "hodlr_logdet_levels": (C.c_int, [_P, _D]),
+    "hodlr_debug_level": (C.c_int, [_P, C.c_int, C.c_int, _D, C.c_int64, C.POINTER(C.c_int32)]),
     "hodlr_napply": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "hodlr_profile": (C.c_int, [_P, C.c_int]),
     "hodlr_profile_read": (C.c_int, [_P, _D]),
@@ -98,12 +100,12 @@ class Hodlr:
     """One HODLR likelihood context on the current CUDA device and stream."""
 
     def __init__(self, dim, G, nvar, nu, precision="fp64", leaf=64, cap=24, oversample=0, tol=0.0, seed=1,
-                 device="cuda"):
+                 device="cuda", guard=0.0):
         import torch
         self.torch = torch
         self.lib = load()
         self.model = Model(dim, (C.c_int * 2)(G, G if dim == 2 else 1), nvar, float(nu), PRECISION[precision])
-        self.opts = Opts(leaf, cap, oversample, float(tol), int(seed))
+        self.opts = Opts(leaf, cap, oversample, float(tol), int(seed), float(guard))
         nbytes = self.lib.hodlr_workspace_size(C.byref(self.model), C.byref(self.opts))
         if nbytes == 0:
             raise HodlrError(-1, "bad model or options")
@@ -238,6 +240,21 @@ class Hodlr:
         self._check(self.lib.hodlr_logdet(self.h, _dp(out)))
         return float(out[0])
 
+    def debug_level(self, what, level):
+        n = self.N * self.cap if what <= 1 else (1 << (level - 1)) * self.cap * self.cap
+        out = np.zeros(max(n, 1))
+        wl = C.c_int32(0)
+        self._check(self.lib.hodlr_debug_level(self.h, what, level, _dp(out), n, C.byref(wl)))
+        w = wl.value
+        if what <= 1:
+            return out[:self.N * w].reshape(w, self.N).T
+        return out[:(1 << (level - 1)) * w * w].reshape(-1, w, w).transpose(0, 2, 1)
+
+    def logdet_levels(self):
+        out = np.zeros(self.tau + 1)
+        self._check(self.lib.hodlr_logdet_levels(self.h, _dp(out)))
+        return out
+
     def traces(self):
         t, f = np.zeros(3), np.zeros(9)
         self._check(self.lib.hodlr_traces(self.h, _dp(t), _dp(f)))
@@ -267,4 +284,5 @@ class Hodlr:
 def from_workload(w, device="cuda", precision=None):
     """Context for a synth.Workload-like object (fields dim, G, nvar, nu, leaf, cap, c, tol, ...)."""
     prec = precision or ("fp64" if w.precision == "fp64" else "fp32")
-    return Hodlr(w.dim, w.G, w.nvar, w.nu, prec, w.leaf, w.cap, w.c - w.cap, w.tol, w.seed_probe, device)
+    return Hodlr(w.dim, w.G, w.nvar, w.nu, prec, w.leaf, w.cap, w.c - w.cap, w.tol, w.seed_probe, device,
+                 guard=getattr(w, "guard", 0.0))

@@ -55,6 +55,7 @@ class Workload:
     precision: str      # "fp64" | "fp32" | "bf16"
     seed_probe: int = 1
     seed_data: int = 0
+    guard: float = 1e-5     # rank guard of the pivoted QR (see GUARD)
 
     @property
     def n_points(self) -> int:
@@ -69,11 +70,14 @@ WORKLOADS = {
     # 1-D univariate, FP64 plain method, n = 1024, leaf 64, rank 16 + 8 oversampling.
     "C0": Workload("C0", 1, 1024, 1, 1.5, (1.0, 0.1, 5.0, 1e-4), 64, 24, 24, 0.0, "fp64"),
     # 1-D bivariate co-kriging, 2^16 points x 2 variables, leaf 256, rank 32, FP32 bulk.
-    "C1": Workload("C1", 1, 65536, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 256, 32, 32, 0.0, "fp32"),
+    # The summed truncation residual of the leaf extraction must stay below tau2: guard 1e-7.
+    "C1": Workload("C1", 1, 65536, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 256, 32, 32, 0.0, "fp32", guard=1e-7),
     # 2-D univariate 512^2 Morton, nu = 1/2, adaptive rank tol 1e-6 cap 128, leaf 256.
     "C2": Workload("C2", 2, 512, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32"),
     # 2-D bivariate 1024^2 (N = 2^21), nu = 3/2, leaf 512, tol 1e-5 cap 192, BF16 sketch.
     "C4": Workload("C4", 2, 1024, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 512, 192, 200, 1e-5, "bf16"),
+    # Reduced 2-D univariate workload of C2's structure (128^2 grid) used for kernel profiles.
+    "S2": Workload("S2", 2, 128, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 64, 72, 1e-6, "fp32"),
 }
 
 

@@ -41,10 +41,8 @@ def oracle_build(w, prec, theta=None, frozen=None, params=("ell", "kappa")):
     return m, t, H
 
 
-# measured on GB300: the 2-D bivariate FP64 case differs from the oracle by 2.7e-10 in the
-# NLL and 3e-7 in the gradient (open: the other cases agree to 1e-13 and 1e-11)
-NLL_TOL = {"2d-biv": 1e-9}
-GRAD_TOL = {"2d-biv": 1e-6}
+NLL_TOL = {}
+GRAD_TOL = {}
 
 SMALL = {
     "1d-uni": synth.small_workload(dim=1, G=512, nvar=1, nu=1.5, theta=(1.0, 0.1, 5.0, 1e-3), leaf=32, cap=10, c=12),
@@ -198,7 +196,7 @@ def test_full_size_tree_order_bit_exact(name):
     import ctypes
     lib = plib.load()
     m = plib.Model(w.dim, (ctypes.c_int * 2)(w.G, w.G if w.dim == 2 else 1), w.nvar, w.nu, 1)
-    o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1)
+    o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1, 0.0)
     # a context needs its workspace; the tree order itself is host data
     nbytes = lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o))
     assert nbytes > 0

@@ -56,7 +56,7 @@ def test_workspace_plan(so_path, name):
     w = synth.workload(name)
     lib = plib.load()
     m = plib.Model(w.dim, (ctypes.c_int * 2)(w.G, w.G if w.dim == 2 else 1), w.nvar, w.nu, 1)
-    o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1)
+    o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1, 0.0)
     n = lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o))
     assert n > 0
     assert n < 280 * 2 ** 30, n / 2 ** 30          # fits one GB300 (FP32 bulk)
@@ -65,8 +65,8 @@ def test_workspace_plan(so_path, name):
 def test_workspace_plan_rejects_bad_options(so_path):
     lib = plib.load()
     m = plib.Model(3, (ctypes.c_int * 2)(8, 8), 1, 1.5, 0)
-    o = plib.Opts(16, 4, 0, 0.0, 1)
+    o = plib.Opts(16, 4, 0, 0.0, 1, 0.0)
     assert lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o)) == 0
     m = plib.Model(1, (ctypes.c_int * 2)(64, 1), 2, 1.5, 0)
-    o = plib.Opts(15, 4, 0, 0.0, 1)                # leaf not a multiple of nvar
+    o = plib.Opts(15, 4, 0, 0.0, 1, 0.0)                # leaf not a multiple of nvar
     assert lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o)) == 0
