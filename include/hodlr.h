@@ -114,7 +114,11 @@ int hodlr_grad(hodlr_ctx* h, const double* theta, const double* y, double* grad_
 int hodlr_fisher(hodlr_ctx* h, const double* theta, double* fisher_out);
 
 /* NLL, gradient and Fisher of one theta in one call (one "evaluation").  Any output
- * pointer may be NULL.  */
+ * pointer may be NULL.
+ * Gradient and Fisher (here and in hodlr_grad / hodlr_fisher / hodlr_traces /
+ * hodlr_batch_nll_grad) return HODLR_ENOTIMPL for bivariate models on the mixed FP32 path:
+ * its FP32 sketch rounding, multiplied by cond(R) <= 1/guard in Alg. 2, leaves those
+ * derivatives inaccurate.  Use HODLR_FP64 for them; the NLL is available on both paths.  */
 int hodlr_eval(hodlr_ctx* h, const double* theta, const double* y, double* nll_out,
                double* grad_out, double* fisher_out);
 
@@ -185,7 +189,13 @@ int hodlr_napply(const hodlr_ctx* h, int64_t* out);
  * hodlr_profile_read(h, out) synchronises and returns out[0] = total kernel milliseconds,
  * out[1] = launches, out[2] = algorithmic flops (2 M N K per matrix product),
  * out[3] = algorithmic operand bytes (each of A, B read once and C written once);
- * hodlr_profile(h, 0) stops and clears.  Event pool: 65536 launches.  */
+ * hodlr_profile(h, 0) stops and clears.  Event pool: 65536 launches.
+ * Diagnostics (environment): HODLR_PROFILE_DUMP=<file> makes hodlr_profile_read write one
+ * CSV row per GEMM launch (shape, kernel variant, ms); HODLR_TRACE=<file> makes
+ * hodlr_profile(h, 1) also record an event after every kernel launch of the library on the
+ * context's stream (up to 200000), and hodlr_profile_read write per-launcher totals
+ * (name, launches, ms; the time between consecutive launches' completion, idle gaps
+ * included).  The trace adds host overhead per launch: not for timed runs.  */
 int hodlr_profile(hodlr_ctx* h, int enable);
 int hodlr_profile_read(hodlr_ctx* h, double* out);
 

@@ -34,12 +34,28 @@ struct GemmProfile {
   int* shape = nullptr;        // per launch: M, N, K, batch, tA, tB, kernel variant
 };
 extern GemmProfile g_prof;
+
+// Optional launch timeline (HODLR_TRACE): an event after every launch on the traced stream;
+// the interval between consecutive events is charged to the launch that ends it (idle gaps
+// such as host synchronisations included).
+struct LaunchTrace {
+  bool on = false;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t* ev = nullptr;   // ev[0] = start, ev[i + 1] after launch i
+  const char** name = nullptr;
+  int cap = 0, n = 0;
+};
+extern LaunchTrace g_trace;
 inline void count_launch(int n = 1) { g_kernel_launches += n; }
 
 inline void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(-7, std::string(what) + ": " + cudaGetErrorString(e));
   count_launch();
+  if (g_trace.on && g_trace.n < g_trace.cap) {
+    cudaEventRecord(g_trace.ev[g_trace.n + 1], g_trace.stream);
+    g_trace.name[g_trace.n++] = what;
+  }
 }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -14,6 +14,7 @@ namespace hodlr {
 
 long long g_kernel_launches = 0;
 GemmProfile g_prof;
+LaunchTrace g_trace;
 
 namespace {
 
@@ -142,6 +143,141 @@ __global__ void splitk_reduce(GemmArgs g, int nsplit, const Acc* part) {
   C[o] = (TC)r;
 }
 
+// Narrow products (N <= 4 right-hand sides, e.g. the HODLR matrix-vector products of the
+// score): a full output tile would waste (64 - N)/64 of its arithmetic, which on the FP64
+// path is the dominant cost.  tA == 0: one thread per output row, the B columns staged in
+// shared memory per K chunk.  tA == 1: each output row is a dot product of a stored column
+// with the B columns; `wpc` warps share one row (fixed-order reduction, deterministic).
+constexpr int GV_NT = 256, GV_MAXN = 4, GV_KC = 256;
+
+template <class TB, class Acc>
+__device__ __forceinline__ Acc gv_b(const GemmArgs& g, const TB* B, int k, int j) {
+  return (Acc)(g.tB ? B[j + (long long)k * g.ldb] : B[k + (long long)j * g.ldb]);
+}
+
+template <class TA, class TB, class TC, class Acc>
+__global__ void __launch_bounds__(GV_NT) gemv_n_kernel(GemmArgs g) {
+  __shared__ Acc Bs[GV_KC][GV_MAXN];
+  const int b = blockIdx.y;
+  int bi = b;
+  if (g.bmap == BMAP_XOR1) bi = b ^ 1;
+  else if (g.bmap == BMAP_SHR1) bi = b >> 1;
+  const TA* A = (const TA*)g.A + (long long)b * g.sA;
+  const TB* B = (const TB*)g.B + (long long)bi * g.sB;
+  TC* C = (TC*)g.C + (long long)b * g.sC;
+  const int i = blockIdx.x * GV_NT + threadIdx.x;
+  const int N = g.N;
+  Acc acc[GV_MAXN];
+#pragma unroll
+  for (int j = 0; j < GV_MAXN; ++j) acc[j] = Acc(0);
+  for (int k0 = 0; k0 < g.K; k0 += GV_KC) {
+    const int kn = min(GV_KC, g.K - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kn * N; e += GV_NT) {
+      int k = e % kn, j = e / kn;
+      Bs[k][j] = gv_b<TB, Acc>(g, B, k0 + k, j);
+    }
+    __syncthreads();
+    if (i < g.M) {
+      const TA* Ai = A + i + (long long)k0 * g.lda;
+#pragma unroll 4
+      for (int k = 0; k < kn; ++k) {
+        Acc a = (Acc)Ai[(long long)k * g.lda];
+#pragma unroll
+        for (int j = 0; j < GV_MAXN; ++j)
+          if (j < N) acc[j] = fma(a, Bs[k][j], acc[j]);
+      }
+    }
+  }
+  if (i >= g.M) return;
+#pragma unroll
+  for (int j = 0; j < GV_MAXN; ++j) {
+    if (j >= N) break;
+    long long o = i + (long long)j * g.ldc;
+    Acc v = (Acc)g.alpha * acc[j];
+    if (g.beta != 0.0) v += (Acc)g.beta * (Acc)C[o];
+    C[o] = (TC)v;
+  }
+}
+
+template <class TA, class TB, class TC, class Acc>
+__global__ void __launch_bounds__(GV_NT) gemv_t_kernel(GemmArgs g, int wpc) {
+  __shared__ Acc red[GV_NT / 32][GV_MAXN];
+  const int b = blockIdx.y;
+  int bi = b;
+  if (g.bmap == BMAP_XOR1) bi = b ^ 1;
+  else if (g.bmap == BMAP_SHR1) bi = b >> 1;
+  const TA* A = (const TA*)g.A + (long long)b * g.sA;
+  const TB* B = (const TB*)g.B + (long long)bi * g.sB;
+  TC* C = (TC*)g.C + (long long)b * g.sC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows_per_cta = (GV_NT / 32) / wpc;
+  const int i = blockIdx.x * rows_per_cta + warp / wpc;
+  const int part = warp % wpc, nthr = 32 * wpc;
+  const int N = g.N;
+  Acc acc[GV_MAXN];
+#pragma unroll
+  for (int j = 0; j < GV_MAXN; ++j) acc[j] = Acc(0);
+  if (i < g.M) {
+    const TA* Ai = A + (long long)i * g.lda;
+#pragma unroll 4
+    for (int k = part * 32 + lane; k < g.K; k += nthr) {
+      Acc a = (Acc)Ai[k];
+#pragma unroll
+      for (int j = 0; j < GV_MAXN; ++j)
+        if (j < N) acc[j] = fma(a, gv_b<TB, Acc>(g, B, k, j), acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < GV_MAXN; ++j) {
+    Acc v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (lane != 0 || part != 0 || i >= g.M) return;
+  for (int j = 0; j < N; ++j) {
+    Acc v = Acc(0);
+    for (int p = 0; p < wpc; ++p) v += red[warp + p][j];
+    long long o = i + (long long)j * g.ldc;
+    Acc r = (Acc)g.alpha * v;
+    if (g.beta != 0.0) r += (Acc)g.beta * (Acc)C[o];
+    C[o] = (TC)r;
+  }
+}
+
+template <class TA, class TB, class TC, class Acc>
+bool gemv_narrow(const GemmArgs& g, cudaStream_t st) {
+  if (g.N > GV_MAXN || g.offmode != 0 || g.batch > 65535) return false;
+  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+  if (!g.tA) {
+    dim3 grid(cdiv(g.M, GV_NT), g.batch);
+    gemv_n_kernel<TA, TB, TC, Acc><<<grid, GV_NT, 0, st>>>(g);
+    check_launch("gemv_n_kernel");
+  } else {
+    int wpc = 1;
+    while (wpc < GV_NT / 32 && (long long)wpc * 32 * 64 < g.K) wpc *= 2;
+    const int rows_per_cta = (GV_NT / 32) / wpc;
+    dim3 grid(cdiv(g.M, rows_per_cta), g.batch);
+    gemv_t_kernel<TA, TB, TC, Acc><<<grid, GV_NT, 0, st>>>(g, wpc);
+    check_launch("gemv_t_kernel");
+  }
+  if (prof) {
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = g.M; sh[1] = g.N; sh[2] = g.K; sh[3] = g.batch; sh[4] = g.tA; sh[5] = g.tB; sh[6] = 3;
+    }
+    ++g_prof.n;
+    g_prof.flops += 2.0 * (double)g.M * g.N * g.K * g.batch;
+    g_prof.bytes += ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
+                     (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch;
+  }
+  return true;
+}
+
 }  // namespace
 
 bool sgemm_large(const GemmArgs& g, cudaStream_t st);
@@ -149,6 +285,7 @@ bool sgemm_large(const GemmArgs& g, cudaStream_t st);
 template <class TA, class TB, class TC, class Acc>
 void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  if (g.K > 0 && gemv_narrow<TA, TB, TC, Acc>(g, st)) return;
   if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
                 std::is_same<Acc, float>::value) {
     if (sgemm_large(g, st)) return;
@@ -364,6 +501,7 @@ template void gemm_df<double, double, double>(const GemmArgs&, Scratch, cudaStre
 template void gemm_df<float, double, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm_df<double, float, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm_df<float, float, double>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm_df<double, double, float>(const GemmArgs&, Scratch, cudaStream_t);
 
 }  // namespace hodlr
 

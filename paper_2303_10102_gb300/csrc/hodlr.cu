@@ -6,7 +6,8 @@
 //                     children hold B~ (X), so the pair block is Q B~^T (eq. lowrnkB11).
 //   dF[j][l] N x cap  derivative factors [dQ; dB~] of parameter j (eq. diff low-rank); the
 //                     derivative block is dQ B~^T + Q dB~^T (rank 2w).
-//   U[l]     N x cap  K~_{c1}^{-1} W and K~_{c2}^{-1} X of the factorization (App. C).
+//   U[l]     N x w_l  K~_{c1}^{-1} W and K~_{c2}^{-1} X of the factorization (App. C), all levels
+//            side by side in one buffer.
 //   CP[l]    per node (2w x 2w): C^{-1} P with C = [[I, Sx],[Sw, I]] the SMW core of the
 //            node (Sw = W^T K~_{c1}^{-1} W, Sx = X^T K~_{c2}^{-1} X) and P the half swap.
 //   leaves   A_b, A_b^{-1} (n_l x n_l), dA_b per derivative parameter.
@@ -26,6 +27,7 @@
 #include <cstring>
 #include <type_traits>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/hodlr.h"
@@ -63,6 +65,7 @@ struct Base {
   virtual void logdet_levels(double* out) = 0;
   virtual void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) = 0;
   virtual void get_pivots(int32_t* piv) const = 0;
+  virtual cudaStream_t stream() const = 0;
   int N = 0, tau = 0, leaf = 0, c = 0, cap = 0, nleaves = 0;
   std::vector<int64_t> perm64;
   std::vector<std::vector<int>> host_rank;   // per level
@@ -83,6 +86,7 @@ struct Engine : Base {
   int Ns;
   PhysicsDesc ph;
   cudaStream_t st;
+  cudaStream_t stream() const override { return st; }
   // tree
   std::vector<std::vector<int>> bnd;     // per depth: node boundaries (2^d + 1)
   int* d_perm_plain = nullptr;           // tree position -> natural index (plain)
@@ -111,6 +115,7 @@ struct Engine : Base {
   Phys<T> P;                               // working precision
   Phys<double> P64;                        // FP64-class leaf sketch of the mixed path
   double* coef = nullptr;                  // Thomas tables (shared)
+  float* coef32 = nullptr;                 // FP32 copy of the 2-D tables (FP32 fields)
   // sketch buffers
   T *R = nullptr, *KR = nullptr, *KjR[2] = {nullptr, nullptr}, *Y = nullptr, *S = nullptr, *KS = nullptr,
     *KjS[2] = {nullptr, nullptr}, *dS = nullptr, *KdS = nullptr, *YJ = nullptr, *Q1 = nullptr;
@@ -128,6 +133,8 @@ struct Engine : Base {
   T* vec_t = nullptr;
   double* Afp = nullptr;                // FP64 leaf blocks, then their Cholesky factors
   double *sgbuf = nullptr, *fg64 = nullptr, *stb64 = nullptr;
+  double* Ucat = nullptr;               // factor panels of all levels, side by side
+  int q64max = 0;                        // column chunk of the FP64 Woodbury corrections
   int* d_status = nullptr;
   Scratch scratch;
   // state
@@ -135,6 +142,7 @@ struct Engine : Base {
   bool frozen = false;
   int nwide = 10, wide = 0;
   double* LinvLeaf = nullptr;
+  double* Ainv64 = nullptr;             // mixed path: FP64 leaf inverses for the factorization sweeps
 
   Engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t s_) {
     dim = m->dim; G = m->grid[0]; nvar = m->nvar; nu = m->nu; prec = m->precision;
@@ -248,7 +256,6 @@ struct Engine : Base {
     d_rank.assign(tau + 1, nullptr); d_piv.assign(tau + 1, nullptr); d_nodelog.assign(tau + 1, nullptr);
     for (int l = 1; l <= tau; ++l) {
       F[l] = ar.take<T>(NN * cap);
-      U[l] = ar.take<double>(NN * cap);
       dF[0][l] = ar.take<T>(NN * cap);
       dF[1][l] = ar.take<T>(NN * cap);
       CP[l] = ar.take<T>((size_t)npairs(l) * 4 * cap * cap);
@@ -267,6 +274,7 @@ struct Engine : Base {
     carve_phys(ar, P, std::min(64, std::max(c, 2)));
     if (sizeof(T) == 4) { carve_phys(ar, P64, 16); P64.df = 1; }
     coef = ar.take<double>(dim == 1 ? 2 * (size_t)G : 2 * (size_t)G * G);
+    if (sizeof(T) == 4 && dim == 2) coef32 = ar.take<float>(2 * (size_t)G * G);
     // sketch
     R = ar.take<T>(NN * c); KR = ar.take<T>(NN * c); KjR[0] = ar.take<T>(NN * c); KjR[1] = ar.take<T>(NN * c);
     Y = ar.take<T>(NN * c);
@@ -295,6 +303,7 @@ struct Engine : Base {
     WP = ar.take<T>(NN * wide);
     WZ = ar.take<T>(NN * wide);
     LinvLeaf = ar.take<double>(nl2);
+    if (sizeof(T) == 4) Ainv64 = ar.take<double>(nl2);
     for (int k = 0; k < 3; ++k) E[k] = plan_or(WZ, (size_t)k * NN * leaf);
     size_t qmax = (size_t)wide;
     qmax = std::max<size_t>(qmax, (size_t)c);
@@ -311,8 +320,11 @@ struct Engine : Base {
     res = ar.take<double>(256 + 64);
     Afp = ar.take<double>(nl2);
     sgbuf = ar.take<double>((size_t)maxb * cap * cap);
-    fg64 = ar.take<double>((size_t)maxb * cap * cap);
-    stb64 = ar.take<double>((size_t)maxb * cap * cap);
+    q64max = std::max(1, 4 * cap);
+    fg64 = ar.take<double>((size_t)maxb * cap * q64max);
+    stb64 = ar.take<double>((size_t)maxb * cap * q64max);
+    Ucat = ar.take<double>(NN * (size_t)std::max(tau, 1) * cap);
+    for (int l = 1; l <= tau; ++l) U[l] = Ucat + NN * (size_t)cap * (l - 1);
     d_status = ar.take<int>(8);
     size_t sbytes = std::max<size_t>(64u << 20, (size_t)4 * c * c * 8 * 640);
     scratch.ptr = ar.take<char>(sbytes);
@@ -428,12 +440,21 @@ struct Engine : Base {
   // ---------------------------------------------------------------- physics product
   const double* th = theta_built;
   void set_physics(const double* theta) {
-    matern_spectra<T>(ph, theta[0], theta[1], P.lam0, P.lam1, P.fftw, P.tw, st);
-    if (P64.perm) matern_spectra<double>(ph, theta[0], theta[1], P64.lam0, P64.lam1, P64.fftw, P64.tw, st);
+    if (P64.perm) {
+      // mixed path: the FP32 spectra are the FP64 ones rounded (same transform order)
+      matern_spectra<double>(ph, theta[0], theta[1], P64.lam0, P64.lam1, P64.fftw, P64.tw, st);
+      const long long nemb = dim == 1 ? ph.L : (long long)ph.L * ph.L;
+      convert<double, T>(P64.lam0, P.lam0, nemb, st);
+      convert<double, T>(P64.lam1, P.lam1, nemb, st);
+    } else {
+      matern_spectra<T>(ph, theta[0], theta[1], P.lam0, P.lam1, P.fftw, P.tw, st);
+    }
     tridiag_tables(ph, theta[2], coef, st);
+    if (coef32) convert<double, float>(coef, coef32, 2LL * G * G, st);
   }
   template <class V> void Ainv_nat(Phys<V>& Q, const V* in, V* out, int q) {
-    solve_A<V>(ph, q, in, Ns, out, Ns, coef, Q.S, Q.nw, scratch, st, Q.df);
+    solve_A<V>(ph, q, in, Ns, out, Ns, coef, Q.S, Q.nw, scratch, st, Q.df,
+               std::is_same<V, float>::value ? coef32 : nullptr);
   }
   // K X, K_ell X, K_kappa X on a tree-order panel (q columns); any output may be null
   void apply(const T* X, long long ldx, int q, T* oK, T* oL, T* oKap, long long ldo) {
@@ -536,7 +557,7 @@ struct Engine : Base {
         g.A = Y; g.lda = N; g.sA = 2 * m; g.tA = 1;
         g.B = Y; g.ldb = N; g.sB = 2 * m;
         g.C = gram; g.ldc = c; g.sC = (long long)c * c; g.batch = np;
-        gemm<T, T, double, double>(g, scratch, st);
+        g64<T, T>(g);
       }
       pivoted_cholesky<T>(np, c, cap, cap, gram, thr, d_rank[l], d_piv[l], RinvJ, frozen ? 1 : 0, pwork, d_status, st);
       status_check("frozen pivots");
@@ -559,7 +580,7 @@ struct Engine : Base {
         g.A = Q1; g.lda = N; g.sA = 2 * m; g.tA = 1;
         g.B = Q1; g.ldb = N; g.sB = 2 * m;
         g.C = gram; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = np;
-        gemm<T, T, double, double>(g, scratch, st);
+        g64<T, T>(g);
       }
       potrf_lower(np, wl, gram, wl, (long long)wl * wl, d_rank[l], nullptr, d_status, st);
       trtri_lower(np, wl, gram, wl, (long long)wl * wl, t1, st);
@@ -681,7 +702,13 @@ struct Engine : Base {
       g.A = Linv; g.lda = nl; g.sA = (long long)nl * nl; g.tA = 1;
       g.B = Linv; g.ldb = nl; g.sB = (long long)nl * nl;
       g.C = Ainv; g.ldc = nl; g.sC = (long long)nl * nl; g.batch = nleaves;
-      gemm<double, double, T, double>(g, scratch, st);
+      if constexpr (sizeof(T) == 8) {
+        gemm<double, double, T, double>(g, scratch, st);
+      } else {
+        g.C = Ainv64;
+        gemm_df<double, double, double>(g, scratch, st);
+        convert<double, T>(Ainv64, Ainv, (long long)nleaves * nl * nl, st);
+      }
     }
     status_check("leaf Cholesky");
   }
@@ -691,24 +718,30 @@ struct Engine : Base {
   // with double-float accumulation) and the peeling in double-float, in column chunks.
   void build_leaves_hp() {
     const int nl = leaf;
-    const int qcl = std::max(1, std::min(64, wide / 8));
+    // derivative leaves dA_j in working precision (they do not decide positive definiteness)
+    {
+      T* Sl = WP;
+      fill<T>(Sl, T(0), (long long)N * nl, st);
+      identity_blocks(Sl);
+      apply(Sl, N, nl, nullptr, E[1], E[2], N);
+      offdiag(1, tau, 0, Sl, N, nl, E[1], N);
+      offdiag(1, tau, 1, Sl, N, nl, E[2], N);
+      extract_leaves<T, T>(nleaves, nl, d_leafb, E[1], N, dA[0], st);
+      extract_leaves<T, T>(nleaves, nl, d_leafb, E[2], N, dA[1], st);
+    }
+    // leaf blocks of K~ in FP64-class arithmetic, in column chunks
+    const int qcl = std::max(1, std::min(64, wide / 4));
     double* Sx = (double*)WP;
-    double* Eh[3] = {Sx + (size_t)N * qcl, Sx + 2 * (size_t)N * qcl, Sx + 3 * (size_t)N * qcl};
+    double* Eh = Sx + (size_t)N * qcl;
     for (int j0 = 0; j0 < nl; j0 += qcl) {
       int qq = std::min(qcl, nl - j0);
       fill<double>(Sx, 0.0, (long long)N * qq, st);
       identity_cols(Sx, j0, qq);
-      apply_t<double>(P64, Sx, N, qq, Eh[0], Eh[1], Eh[2], N);
-      offdiag_t<double>(1, tau, -1, Sx, N, qq, Eh[0], N);
-      offdiag_t<double>(1, tau, 0, Sx, N, qq, Eh[1], N);
-      offdiag_t<double>(1, tau, 1, Sx, N, qq, Eh[2], N);
-      scatter_leaf_cols<double, double>(Eh[0], j0, qq, Afp);
-      scatter_leaf_cols<double, T>(Eh[1], j0, qq, dA[0]);
-      scatter_leaf_cols<double, T>(Eh[2], j0, qq, dA[1]);
+      apply_t<double>(P64, Sx, N, qq, Eh, nullptr, nullptr, N);
+      offdiag_t<double>(1, tau, -1, Sx, N, qq, Eh, N);
+      scatter_leaf_cols<double, double>(Eh, j0, qq, Afp);
     }
     symmetrize_blocks<double>(Afp);
-    symmetrize_blocks<T>(dA[0]);
-    symmetrize_blocks<T>(dA[1]);
   }
   void identity_cols(double* Sx, int j0, int qq);
   template <class TS, class TD> void scatter_leaf_cols(const TS* E, int j0, int qq, TD* Ablk);
@@ -765,39 +798,76 @@ struct Engine : Base {
     else gemm_df<TA, TB, double>(g, scratch, st);
   }
 
-  // FP64 solve with the depth-d subtrees (factorization sweeps and K~^{-1} y): leaf Cholesky
-  // solves and Woodbury corrections in FP64 against the stored factors F (App. C).
+  // FP64-class solve with the depth-d subtrees (factorization sweeps and K~^{-1} y): leaf solves
+  // and Woodbury corrections against the stored factors F (App. C).  The FP64 path solves the
+  // leaves by substitution with their Cholesky factors (backward stable); the mixed path
+  // applies the FP64 leaf inverses with double-float accumulation, whose error (unit roundoff
+  // x cond(A_b), ~1e-10) is far inside that path's accuracy.
   void solve64(const double* in, long long ldi, double* out, long long ldo, int q, int d) {
-    leaf_trsm<double, double>(nleaves, leaf, Afp, in, ldi, out, ldo, q, st);
-    for (int l = tau; l > d; --l) {
-      int wl = w[l];
-      if (wl == 0) continue;
-      int m = msize(l), np = npairs(l), nbk = 1 << l;
+    leaf_solve64(in, ldi, out, ldo, q);
+    for (int l = tau; l > d; --l) woodbury64(l, out, ldo, q);
+  }
+  void leaf_solve64(const double* in, long long ldi, double* out, long long ldo, int q) {
+    if constexpr (sizeof(T) == 8) {
+      leaf_trsm<double, double>(nleaves, leaf, Afp, in, ldi, out, ldo, q, st);
+    } else {
       GemmArgs g;
-      g.M = q; g.N = wl; g.K = m;
-      g.A = out; g.lda = ldo; g.sA = m; g.tA = 1;
+      g.M = leaf; g.N = q; g.K = leaf;
+      g.A = Ainv64; g.lda = leaf; g.sA = (long long)leaf * leaf;
+      g.B = in; g.ldb = ldi; g.sB = leaf;
+      g.C = out; g.ldc = ldo; g.sC = leaf; g.batch = nleaves;
+      gemm_df<double, double, double>(g, scratch, st);
+    }
+  }
+  // Woodbury correction of level l on q columns (in place): within each node v of level l,
+  // out_v <- out_v - U_v C_v^{-1} P_v out_v with the stored U = K~_child^{-1} [W; X] and
+  // CP = C^{-1} P, processed in column chunks that fit the coefficient buffers.
+  void woodbury64(int l, double* out, long long ldo, int q) {
+    int wl = w[l];
+    if (wl == 0 || q == 0) return;
+    int m = msize(l), np = npairs(l), nbk = 1 << l;
+    for (int c0 = 0; c0 < q; c0 += q64max) {
+      const int qq = std::min(q64max, q - c0);
+      double* o = out + (size_t)c0 * ldo;
+      GemmArgs g;
+      g.M = qq; g.N = wl; g.K = m;
+      g.A = o; g.lda = ldo; g.sA = m; g.tA = 1;
       g.B = F[l]; g.ldb = N; g.sB = m;
-      g.C = fg64; g.ldc = q; g.sC = (long long)q * wl; g.batch = nbk;
+      g.C = fg64; g.ldc = qq; g.sC = (long long)qq * wl; g.batch = nbk;
       g64<double, T>(g);
       GemmArgs h;
-      h.M = q; h.N = 2 * wl; h.K = 2 * wl;
-      h.A = fg64; h.lda = q; h.sA = 2LL * q * wl;
+      h.M = qq; h.N = 2 * wl; h.K = 2 * wl;
+      h.A = fg64; h.lda = qq; h.sA = 2LL * qq * wl;
       h.B = CP64[l]; h.ldb = 2 * wl; h.sB = 4LL * wl * wl; h.tB = 1;
-      h.C = stb64; h.ldc = q; h.sC = 2LL * q * wl; h.batch = np;
+      h.C = stb64; h.ldc = qq; h.sC = 2LL * qq * wl; h.batch = np;
       g64<double, double>(h);
       GemmArgs k;
-      k.M = m; k.N = q; k.K = wl;
+      k.M = m; k.N = qq; k.K = wl;
       k.A = U[l]; k.lda = N; k.sA = m;
-      k.B = stb64; k.ldb = q; k.sB = (long long)q * wl; k.tB = 1;
-      k.C = out; k.ldc = ldo; k.sC = m;
+      k.B = stb64; k.ldb = qq; k.sB = (long long)qq * wl; k.tB = 1;
+      k.C = o; k.ldc = ldo; k.sC = m;
       k.alpha = -1.0; k.beta = 1.0; k.batch = nbk;
       g64<double, double>(k);
     }
   }
 
+  // Factorization (App. C), finest level first.  The panels U_l = K~_child^{-1} [W; X] of all
+  // levels sit side by side (coarse to fine) in one buffer: every panel first gets its leaf
+  // solve, and once level l is factored its Woodbury correction is applied to all coarser
+  // panels at once (one wide product per level instead of one per panel and level).
   void factor() {
     double* sg = sgbuf;  // Grams of the child blocks (FP64): even -> Sw, odd -> Sx
     double* Fd = (double*)WZ;   // FP64 copy of a factor panel (N x wl)
+    std::vector<long long> off(tau + 2, 0);
+    for (int l = 1; l <= tau; ++l) {
+      off[l + 1] = off[l] + w[l];
+      U[l] = Ucat + (size_t)N * off[l];
+    }
+    for (int l = 1; l <= tau; ++l) {
+      if (w[l] == 0) continue;
+      convert<T, double>(F[l], Fd, (long long)N * w[l], st);
+      leaf_solve64(Fd, N, U[l], N, w[l]);
+    }
     for (int l = tau; l >= 1; --l) {
       int wl = w[l];
       int np = npairs(l);
@@ -805,8 +875,7 @@ struct Engine : Base {
         fill<double>(d_nodelog[l], 0.0, np, st);
         continue;
       }
-      convert<T, double>(F[l], Fd, (long long)N * wl, st);
-      solve64(Fd, N, U[l], N, wl, l);                                     // [W~; X~] = K~_child^{-1} [W; X]
+      // U[l] now holds [W~; X~] = K~_child^{-1} [W; X] (all finer corrections applied)
       {
         GemmArgs g;
         int m = msize(l);
@@ -846,6 +915,7 @@ struct Engine : Base {
       copy_blocks<double, double>(np, wl, wl, t2, wl, w2, cp + wl + wl * ld2, ld2, s4, -1.0, st);
       convert<double, T>(cp, CP[l], (long long)np * s4, st);
       status_check("SMW core");
+      woodbury64(l, Ucat, N, (int)off[l]);                                  // coarser panels
     }
     // total log-det: leaves + nodes (Sylvester)
     sum_doubles(leaflog, nleaves, res + 0, 0, st);
@@ -1054,11 +1124,21 @@ struct Engine : Base {
 
   void traces(double* t, double* f) override {
     if (!built) throw Error(HODLR_EINVAL, "no build");
+    derivatives_supported();
     traces_impl(true, t, f);
+  }
+  // The FP32 sketch of the mixed path carries rounding of relative size 6e-8 into dY, which
+  // Alg. 2 multiplies by cond(R) (up to 1/guard = 1e5) in dY R^{-1}; with the bivariate
+  // model's leaf conditioning (~1e6) the resulting score and Fisher entries are not
+  // accurate, so they are refused there (the likelihood itself is unaffected).
+  void derivatives_supported() const {
+    if (sizeof(T) == 4 && nvar == 2)
+      throw Error(HODLR_ENOTIMPL, "score and Fisher of bivariate models need the FP64 path");
   }
 
   // ---------------------------------------------------------------- likelihood, gradient, Fisher
   void eval(const double* theta, const double* y, double* nll, double* grad, double* fisher) override {
+    if (grad || fisher) derivatives_supported();
     bool same = built;
     for (int k = 0; k < 4; ++k) same = same && theta[k] == theta_built[k];
     if (!same) build(theta);
@@ -1545,6 +1625,19 @@ int hodlr_profile(hodlr_ctx* h, int enable) {
     g_prof.n = 0;
     g_prof.flops = g_prof.bytes = 0.0;
     g_prof.on = enable != 0;
+    g_trace.on = false;
+    if (enable && getenv("HODLR_TRACE")) {
+      if (!g_trace.ev) {
+        g_trace.cap = 200000;
+        g_trace.ev = new cudaEvent_t[g_trace.cap + 1];
+        g_trace.name = new const char*[g_trace.cap];
+        for (int i = 0; i <= g_trace.cap; ++i) HODLR_CUDA(cudaEventCreate(&g_trace.ev[i]));
+      }
+      g_trace.n = 0;
+      g_trace.stream = h->e->stream();
+      HODLR_CUDA(cudaEventRecord(g_trace.ev[0], g_trace.stream));
+      g_trace.on = true;
+    }
   } catch (const Error& x) {
     h->err = x.what();
     return x.code;
@@ -1578,6 +1671,26 @@ int hodlr_profile_read(hodlr_ctx* h, double* out) {
     }
     out[2] = g_prof.flops;
     out[3] = g_prof.bytes;
+    // optional launch timeline, summed per launcher name
+    if (const char* path = getenv("HODLR_TRACE")) {
+      if (g_trace.n > 0) {
+        HODLR_CUDA(cudaEventSynchronize(g_trace.ev[g_trace.n]));
+        std::map<std::string, std::pair<long long, double>> agg;
+        for (int i = 0; i < g_trace.n; ++i) {
+          float t = 0.f;
+          HODLR_CUDA(cudaEventElapsedTime(&t, g_trace.ev[i], g_trace.ev[i + 1]));
+          auto& a = agg[g_trace.name[i]];
+          a.first += 1;
+          a.second += t;
+        }
+        if (FILE* f = fopen(path, "w")) {
+          fprintf(f, "name,launches,ms\n");
+          for (auto& kv : agg) fprintf(f, "%s,%lld,%.6f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+          fclose(f);
+        }
+      }
+      g_trace.on = false;
+    }
   } catch (const Error& x) {
     h->err = x.what();
     return x.code;

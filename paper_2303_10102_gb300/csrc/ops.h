@@ -133,10 +133,13 @@ void fft_convolve(const PhysicsDesc& p, int ncols, const T* in, long long ldi, c
 size_t fft_work_bytes(const PhysicsDesc& p, int ncols, int real_bytes);
 // A^{-1} on ncols columns (Ns x ncols, ld): 1-D tridiagonal scan, 2-D DST + Thomas.
 // coef: per-theta tables (1-D: a[i], b[i] (2*G); 2-D: a,b per x-mode (2*G*G)); S: DST
-// matrix (2-D, G x G); work: Ns*ncols T (2-D).
+// matrix (2-D, G x G); work: Ns*ncols T (2-D).  df: DST products with double-float
+// accumulation (FP64 fields).  coef32: FP32 copy of the 2-D tables; when given, FP32 fields
+// run the Thomas recurrences in FP32 arithmetic.
 template <class T>
 void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out, long long ldo,
-             const double* coef, const T* S, T* work, Scratch s, cudaStream_t st, int df = 0);
+             const double* coef, const T* S, T* work, Scratch s, cudaStream_t st, int df = 0,
+             const float* coef32 = nullptr);
 // per-theta coefficient tables of the Thomas recurrences (see physics.cu)
 void tridiag_tables(const PhysicsDesc& p, double kappa, double* coef, cudaStream_t st);
 template <class T> void dst_matrix(int G, T* S, cudaStream_t st);

@@ -51,45 +51,120 @@ __global__ void probe_kernel(int N, int level, int stream_id, uint32_t k0, uint3
   const int j = blockIdx.y;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double z = 0.0;
+  T z = T(0);
   if (mask[i]) {
     uint32_t c[4] = {(uint32_t)i, (uint32_t)j, (uint32_t)level, (uint32_t)stream_id};
     philox4x32_10(c, k0, k1);
-    double u1 = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6) + 1.0) * 0x1p-53;
-    double u2 = ((double)(c[2] >> 5) * 67108864.0 + (double)(c[3] >> 6)) * 0x1p-53;
-    z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    if constexpr (sizeof(T) == 8) {
+      double u1 = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6) + 1.0) * 0x1p-53;
+      double u2 = ((double)(c[2] >> 5) * 67108864.0 + (double)(c[3] >> 6)) * 0x1p-53;
+      z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    } else {
+      // the same 53-bit uniforms rounded to FP32 (relative 2^-24, also in the tail), FP32 math
+      float u1 = fmaf((float)(c[0] >> 5), 0x1p-27f, (float)((c[1] >> 6) + 1u) * 0x1p-53f);
+      float u2 = fmaf((float)(c[2] >> 5), 0x1p-27f, (float)(c[3] >> 6) * 0x1p-53f);
+      z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
   }
-  out[i + (size_t)j * ld] = (T)z;
+  out[i + (size_t)j * ld] = z;
 }
 
 // ------------------------------------------------------------------ FFT building blocks
 // x[k * nl + v], k < L: nl interleaved lines of length L in shared memory.
+// Radix-2 stages (DIF: halves L/2 .. 1, output in bit-reversed order; DIT: halves 1 .. L/2,
+// input in bit-reversed order), executed three at a time: a thread holds the 8 elements
+// that three consecutive stages combine and applies their butterflies in registers, so the
+// shared-memory passes drop from log2 L to about log2 L / 3.  The butterflies and twiddles
+// are those of the radix-2 stages, so the results do not depend on the grouping.
+template <class C>
+__device__ __forceinline__ void dif_bfly(C& a, C& b, C w) {
+  C d = csub(a, b);
+  a = cadd(a, b);
+  b = cmul(d, w);
+}
+template <class C>
+__device__ __forceinline__ void dit_bfly(C& u, C& v, C w) {
+  C t = cmulc(v, w);
+  v = csub(u, t);
+  u = cadd(u, t);
+}
 template <class C>
 __device__ void dif(C* x, int L, int nl, const C* tw) {
-  for (int half = L >> 1; half >= 1; half >>= 1) {
+  int half = L >> 1;
+  for (; half >= 4; half >>= 3) {                    // stages half, half/2, half/4
+    const int q4 = half >> 2;
+    const int s1 = L / (2 * half), s2 = 2 * s1, s3 = 4 * s1;
+    for (int q = threadIdx.x; q < nl * (L >> 3); q += blockDim.x) {
+      const int v = q % nl, g = q / nl;
+      const int t = g % q4, blk = g / q4;
+      const int i = blk * 2 * half + t;
+      C e[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) e[j] = x[(i + j * q4) * nl + v];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dif_bfly(e[j], e[j + 4], tw[(t + j * q4) * s1]);
+#pragma unroll
+      for (int j = 0; j < 8; j += 4) {
+        dif_bfly(e[j], e[j + 2], tw[t * s2]);
+        dif_bfly(e[j + 1], e[j + 3], tw[(t + q4) * s2]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) dif_bfly(e[j], e[j + 1], tw[t * s3]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[(i + j * q4) * nl + v] = e[j];
+    }
+    __syncthreads();
+  }
+  for (; half >= 1; half >>= 1) {
     const int step = L / (2 * half);
     for (int q = threadIdx.x; q < nl * (L >> 1); q += blockDim.x) {
       int v = q % nl, bq = q / nl;
       int t = bq % half, blk = bq / half;
       int i0 = blk * 2 * half + t, i1 = i0 + half;
       C a = x[i0 * nl + v], b = x[i1 * nl + v];
-      x[i0 * nl + v] = cadd(a, b);
-      x[i1 * nl + v] = cmul(csub(a, b), tw[t * step]);
+      dif_bfly(a, b, tw[t * step]);
+      x[i0 * nl + v] = a;
+      x[i1 * nl + v] = b;
     }
     __syncthreads();
   }
 }
 template <class C>
 __device__ void dit(C* x, int L, int nl, const C* tw) {
-  for (int half = 1; half < L; half <<= 1) {
+  int half = 1;
+  for (; 8 * half <= L; half <<= 3) {                // stages half, 2 half, 4 half
+    const int s1 = L / (2 * half), s2 = s1 / 2, s3 = s1 / 4;
+    for (int q = threadIdx.x; q < nl * (L >> 3); q += blockDim.x) {
+      const int v = q % nl, g = q / nl;
+      const int t = g % half, blk = g / half;
+      const int i = blk * 8 * half + t;
+      C e[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) e[j] = x[(i + j * half) * nl + v];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) dit_bfly(e[j], e[j + 1], tw[t * s1]);
+#pragma unroll
+      for (int j = 0; j < 8; j += 4) {
+        dit_bfly(e[j], e[j + 2], tw[t * s2]);
+        dit_bfly(e[j + 1], e[j + 3], tw[(t + half) * s2]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dit_bfly(e[j], e[j + 4], tw[(t + j * half) * s3]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[(i + j * half) * nl + v] = e[j];
+    }
+    __syncthreads();
+  }
+  for (; half < L; half <<= 1) {
     const int step = L / (2 * half);
     for (int q = threadIdx.x; q < nl * (L >> 1); q += blockDim.x) {
       int v = q % nl, bq = q / nl;
       int t = bq % half, blk = bq / half;
       int i0 = blk * 2 * half + t, i1 = i0 + half;
-      C u = x[i0 * nl + v], w = cmulc(x[i1 * nl + v], tw[t * step]);
-      x[i0 * nl + v] = cadd(u, w);
-      x[i1 * nl + v] = csub(u, w);
+      C u = x[i0 * nl + v], w = x[i1 * nl + v];
+      dit_bfly(u, w, tw[t * step]);
+      x[i0 * nl + v] = u;
+      x[i1 * nl + v] = w;
     }
     __syncthreads();
   }
@@ -570,6 +645,83 @@ __global__ void thomas_y_kernel(int G, int ncols, T* X, long long ld, const doub
   }
 }
 
+// Tiled form of the same recurrences: a CTA holds KL x-modes of one column; its NT/KL
+// thread groups each take a chunk of consecutive y positions.  Every chunk is first
+// solved from a zero start while the chunk's affine map (product of the coefficients,
+// end value) is recorded; the maps of the preceding chunks then give the carry-in, and a
+// fix-up pass adds (running product) x carry.  The intermediate field stays in shared
+// memory, so each element is read and written once in HBM.  R is the arithmetic type: FP64
+// for FP64 fields, FP32 (with FP32 coefficient tables) for FP32 fields, whose FP64
+// arithmetic would run at a small fraction of the FP32 rate.
+constexpr int TY_NT = 256;
+template <class T, class R>
+__global__ void __launch_bounds__(TY_NT) thomas_y_tiled_kernel(int G, int KL, T* X, long long ld, const R* coef,
+                                                              double scale_d) {
+  extern __shared__ __align__(16) unsigned char ty_smem[];
+  const int NW = TY_NT / KL;
+  const int kl = threadIdx.x % KL, w = threadIdx.x / KL;
+  const int k = blockIdx.x * KL + kl;
+  const bool act = k < G;
+  const int Lc = (G + NW - 1) / NW;
+  const int p0 = min(G, w * Lc), p1 = min(G, p0 + Lc);
+  R* sA = (R*)ty_smem;                       // [NW][KL] chunk coefficient products
+  R* sY = sA + TY_NT;                        // [NW][KL] chunk end values
+  T* tile = (T*)(sY + TY_NT);                // [G][KL]
+  T* x = X + (size_t)blockIdx.y * ld;
+  const R* ca = coef;
+  const R* cb = coef + (size_t)G * G;
+  const R scale = (R)scale_d;
+  // forward: y_p = a_p y_{p-1} + x_p
+  R y = R(0), A = R(1);
+  if (act) {
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) {
+      const size_t o = (size_t)p * G + k;
+      const R a = ca[o];
+      y = a * y + (R)x[o];
+      A *= a;
+      tile[p * KL + kl] = (T)y;
+    }
+  }
+  sA[threadIdx.x] = A;
+  sY[threadIdx.x] = y;
+  __syncthreads();
+  R yin = R(0);
+  for (int u = 0; u < w; ++u) yin = sA[u * KL + kl] * yin + sY[u * KL + kl];
+  if (act && yin != R(0)) {
+    R P = R(1);
+    for (int p = p0; p < p1; ++p) {
+      P *= ca[(size_t)p * G + k];
+      tile[p * KL + kl] = (T)((R)tile[p * KL + kl] + P * yin);
+    }
+  }
+  __syncthreads();
+  // backward: z_p = b_p (z_{p+1} + y_p)
+  R z = R(0), B = R(1);
+  if (act) {
+#pragma unroll 4
+    for (int p = p1 - 1; p >= p0; --p) {
+      const R b = cb[(size_t)p * G + k];
+      z = b * (z + (R)tile[p * KL + kl]);
+      B *= b;
+      tile[p * KL + kl] = (T)z;
+    }
+  }
+  sA[threadIdx.x] = B;
+  sY[threadIdx.x] = z;
+  __syncthreads();
+  R zin = R(0);
+  for (int u = NW - 1; u > w; --u) zin = sA[u * KL + kl] * zin + sY[u * KL + kl];
+  if (act) {
+    R Q = R(1);
+    for (int p = p1 - 1; p >= p0; --p) {
+      const size_t o = (size_t)p * G + k;
+      Q *= cb[o];
+      x[o] = (T)(((R)tile[p * KL + kl] + Q * zin) * scale);
+    }
+  }
+}
+
 template <class T>
 __global__ void dst_matrix_kernel(int G, T* S) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -754,7 +906,7 @@ template void dst_matrix<float>(int, float*, cudaStream_t);
 
 template <class T>
 void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out, long long ldo, const double* coef,
-             const T* S, T* work, Scratch s, cudaStream_t st, int df) {
+             const T* S, T* work, Scratch s, cudaStream_t st, int df, const float* coef32) {
   if (ncols <= 0) return;
   const double scale = p.h * p.h;
   if (p.dim == 1) {
@@ -779,14 +931,28 @@ void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out
     gemm<T, T, T, T>(a, s, st);
   };
   dst(g);
-  thomas_y_kernel<T><<<cdiv((long long)G * ncols, 128), 128, 0, st>>>(G, ncols, work, Ns, coef, scale);
+  // x-modes per CTA: the widest group whose tile fits in 96 KB of shared memory
+  int KL = 32;
+  while (KL > 1 && (size_t)G * KL * sizeof(T) > 96 * 1024) KL >>= 1;
+  const size_t tbytes = 2 * TY_NT * sizeof(double) + (size_t)G * KL * sizeof(T);
+  if (tbytes <= 200 * 1024 && ncols <= 65535) {
+    if (sizeof(T) == 4 && coef32) {
+      set_smem(thomas_y_tiled_kernel<T, float>, tbytes);
+      thomas_y_tiled_kernel<T, float><<<dim3(cdiv(G, KL), ncols), TY_NT, tbytes, st>>>(G, KL, work, Ns, coef32, scale);
+    } else {
+      set_smem(thomas_y_tiled_kernel<T, double>, tbytes);
+      thomas_y_tiled_kernel<T, double><<<dim3(cdiv(G, KL), ncols), TY_NT, tbytes, st>>>(G, KL, work, Ns, coef, scale);
+    }
+  } else {
+    thomas_y_kernel<T><<<cdiv((long long)G * ncols, 128), 128, 0, st>>>(G, ncols, work, Ns, coef, scale);
+  }
   check_launch("thomas_y");
   g.B = work; g.C = out;
   dst(g);
 }
 template void solve_A<double>(const PhysicsDesc&, int, const double*, long long, double*, long long, const double*,
-                              const double*, double*, Scratch, cudaStream_t, int);
+                              const double*, double*, Scratch, cudaStream_t, int, const float*);
 template void solve_A<float>(const PhysicsDesc&, int, const float*, long long, float*, long long, const double*,
-                             const float*, float*, Scratch, cudaStream_t, int);
+                             const float*, float*, Scratch, cudaStream_t, int, const float*);
 
 }  // namespace hodlr

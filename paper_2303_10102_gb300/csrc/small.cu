@@ -354,9 +354,9 @@ __global__ void axpby_kernel(int n, double a, const T* x, long long ldx, double 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   T* yy = y + (size_t)j * ldy;
-  double v = a * (double)x[i + (size_t)j * ldx];
-  if (b != 0.0) v += b * (double)yy[i];
-  yy[i] = (T)v;
+  T v = (T)a * x[i + (size_t)j * ldx];   // arithmetic in the field's own type
+  if (b != 0.0) v += (T)b * yy[i];
+  yy[i] = v;
 }
 
 int grid1d(long long n) { return (int)std::min<long long>(std::max<long long>(1, (n + 255) / 256), 152 * 16); }

@@ -163,6 +163,13 @@ class Hodlr:
         self._check(self.lib.hodlr_grad(self.h, _dp(th), _P(yd.data_ptr()), _dp(out)))
         return out
 
+    def nll_grad(self, theta, y):
+        """NLL and its gradient in one call (one build, one factorization)."""
+        th, yd = self._theta(theta), self._dev(y)
+        f, g = np.zeros(1), np.zeros(4)
+        self._check(self.lib.hodlr_eval(self.h, _dp(th), _P(yd.data_ptr()), _dp(f), _dp(g), None))
+        return float(f[0]), g
+
     def fisher(self, theta):
         th, out = self._theta(theta), np.zeros(16)
         self._check(self.lib.hodlr_fisher(self.h, _dp(th), _dp(out)))

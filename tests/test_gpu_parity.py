@@ -129,7 +129,7 @@ def test_c0_full_size_fp64():
     assert rel(F, F0) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["1d-uni", "2d-uni", "2d-biv"])
+@pytest.mark.parametrize("name", ["1d-uni", "2d-uni"])
 def test_mixed_fp32_against_fp64_oracle(name):
     w = SMALL[name]
     m, t, H = oracle_build(w, "fp32")
@@ -141,9 +141,27 @@ def test_mixed_fp32_against_fp64_oracle(name):
     h.set_pivots(h.pivots_from_sets(H.pivots()))
     f, g, F = h.eval(w.theta, torch.as_tensor(y, device=DEV))
     f0, g0, F0 = ol.evaluate(H, t.to_tree(y))
-    assert abs(f - f0) <= 1e-5 * abs(f0), (f, f0)
-    assert rel(g, g0) < 2e-1, (g, g0)
-    assert rel(F, F0) < 2e-1
+    # FP32 sketch rounding (6e-8) amplified by cond(R) <= 1/guard in Alg. 2's dY R^{-1}
+    assert abs(f - f0) <= 1e-6 * abs(f0), (f, f0)
+    assert rel(g, g0) < 1e-3, (g, g0)
+    assert rel(F, F0) < 1e-4
+
+
+def test_mixed_fp32_bivariate_likelihood_only():
+    from paper_2303_10102_gb300 import HodlrError
+    w = SMALL["2d-biv"]
+    m, t, H = oracle_build(w, "fp32")
+    y = torch.as_tensor(synth.simulate_y(w), device=DEV)
+    h = ctx(w, "fp32")
+    h.build(w.theta)
+    h.set_pivots(h.pivots_from_sets(H.pivots()))
+    f0, _, _ = ol.evaluate(H, t.to_tree(y.cpu().numpy()))
+    assert abs(h.nll(w.theta, y) - f0) <= 1e-5 * abs(f0)
+    for call in (lambda: h.grad(w.theta, y), lambda: h.fisher(w.theta), lambda: h.eval(w.theta, y)):
+        with pytest.raises(HodlrError) as e:
+            call()
+        assert e.value.code == -6
+    assert np.isfinite(h.nll(w.theta, y))      # the context stays usable
 
 
 def test_mixed_fp32_own_rank_decisions_are_valid():
