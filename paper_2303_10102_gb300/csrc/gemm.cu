@@ -359,6 +359,7 @@ __device__ __forceinline__ DF df_from(double x) {
   return {h, (float)(x - (double)h)};
 }
 __device__ __forceinline__ DF df_from(float x) { return {x, 0.0f}; }
+__device__ __forceinline__ DF df_from(float2 x) { return {x.x, x.y}; }   // operand already split
 // acc += a * b (double-float), error-free product of the high parts plus the cross terms
 __device__ __forceinline__ DF df_fma(DF acc, DF a, DF b) {
   float p = a.hi * b.hi;
@@ -377,6 +378,7 @@ template <class TA, class TB, class TC>
 __global__ void __launch_bounds__(NT) gemm_df_kernel(GemmArgs g, int nsplit, int kchunk, double* part) {
   __shared__ DF As[BK][BM + 1];
   __shared__ DF Bs[BK][BN + 1];
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;   // tile elements per thread
   const int tid = threadIdx.x;
   const int tx = tid % (BM / TM);
   const int ty = tid / (BM / TM);
@@ -403,24 +405,49 @@ __global__ void __launch_bounds__(NT) gemm_df_kernel(GemmArgs g, int nsplit, int
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = {0.0f, 0.0f};
-  for (int k0 = kb; k0 < ke; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += NT) {
+  // the next tile is fetched into registers while the current one is multiplied
+  DF ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
       int i, k;
       if (!g.tA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
-      int gi = m0 + i, gk = k0 + k;
-      DF v = {0.0f, 0.0f};
-      if (gi < M && gk < ke) v = df_from(g.tA ? A[gk + (long long)gi * g.lda] : A[gi + (long long)gk * g.lda]);
-      As[k][i] = v;
+      const int gi = m0 + i, gk = k0 + k;
+      ra[r] = (gi < M && gk < ke) ? df_from(g.tA ? A[gk + (long long)gi * g.lda] : A[gi + (long long)gk * g.lda])
+                                  : DF{0.0f, 0.0f};
     }
-    for (int e = tid; e < BK * BN; e += NT) {
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * NT;
       int k, j;
       if (!g.tB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
-      int gj = n0 + j, gk = k0 + k;
-      DF v = {0.0f, 0.0f};
-      if (gj < g.N && gk < ke) v = df_from(g.tB ? B[gj + (long long)gk * g.ldb] : B[gk + (long long)gj * g.ldb]);
-      Bs[k][j] = v;
+      const int gj = n0 + j, gk = k0 + k;
+      rb[r] = (gj < g.N && gk < ke) ? df_from(g.tB ? B[gj + (long long)gk * g.ldb] : B[gk + (long long)gj * g.ldb])
+                                    : DF{0.0f, 0.0f};
     }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
+      int i, k;
+      if (!g.tA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
+      As[k][i] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * NT;
+      int k, j;
+      if (!g.tB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
+      Bs[k][j] = rb[r];
+    }
+  };
+  if (kb < ke) fetch(kb);
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+    stash();
     __syncthreads();
+    if (k0 + BK < ke) fetch(k0 + BK);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       DF a[TM], bb[TN];
@@ -453,6 +480,14 @@ __global__ void __launch_bounds__(NT) gemm_df_kernel(GemmArgs g, int nsplit, int
       }
     }
   }
+}
+
+__global__ void df_split_kernel(const double* x, float2* y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  const float h = (float)v;
+  y[i] = make_float2(h, (float)(v - (double)h));
 }
 
 }  // namespace
@@ -502,6 +537,14 @@ template void gemm_df<float, double, double>(const GemmArgs&, Scratch, cudaStrea
 template void gemm_df<double, float, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm_df<float, float, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm_df<double, double, float>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm_df<float2, float2, double>(const GemmArgs&, Scratch, cudaStream_t);
+template void gemm_df<float2, double, double>(const GemmArgs&, Scratch, cudaStream_t);
+
+void df_split(const double* x, float2* y, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  df_split_kernel<<<cdiv(n, 256), 256, 0, st>>>(x, y, n);
+  check_launch("df_split");
+}
 
 }  // namespace hodlr
 

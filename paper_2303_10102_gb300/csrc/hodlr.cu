@@ -111,6 +111,8 @@ struct Engine : Base {
     V *nx = nullptr, *na = nullptr, *nb = nullptr, *nu = nullptr, *nu2 = nullptr, *ns = nullptr, *ne = nullptr,
       *nt = nullptr, *nw = nullptr;
     int df = 0;                            // 2-D DST products with double-float accumulation
+    float *Shi = nullptr, *Slo = nullptr;  // TF32 split of the FP32 DST matrix (tensor-core products)
+    float2 *Sdf = nullptr, *Xdf = nullptr; // double-float split of the DST matrix and a field panel
   };
   Phys<T> P;                               // working precision
   Phys<double> P64;                        // FP64-class leaf sketch of the mixed path
@@ -236,6 +238,14 @@ struct Engine : Base {
     Q.lam1 = ar.take<V>(nemb);
     Q.tw = ar.take<V>(2 * (size_t)ph.L + 16);
     if (dim == 2) Q.S = ar.take<V>((size_t)G * G);
+    if (dim == 2 && sizeof(V) == 4 && tf32x3_supported(G, G, G, G, G)) {
+      Q.Shi = ar.take<float>((size_t)G * G);
+      Q.Slo = ar.take<float>((size_t)G * G);
+    }
+    if (dim == 2 && sizeof(V) == 8 && sizeof(T) == 4) {   // the FP64-class fields of the mixed path
+      Q.Sdf = ar.take<float2>((size_t)G * G);
+      Q.Xdf = ar.take<float2>((size_t)Ns * qc);
+    }
     Q.fftw_bytes = std::max(fft_work_bytes(ph, qc, sizeof(V)), nemb * (sizeof(V) * 3) + 512);
     Q.fftw = ar.take<char>(Q.fftw_bytes);
     size_t nat = (size_t)nvar * Ns * qc;
@@ -356,6 +366,8 @@ struct Engine : Base {
     }
     HODLR_CUDA(cudaMemcpyAsync(Q.perm, pv.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
     if (dim == 2) dst_matrix<V>(G, Q.S, st);
+    if (Q.Shi) tf32_split((const float*)Q.S, Q.Shi, Q.Slo, (long long)G * G, st);
+    if (Q.Sdf) df_split((const double*)Q.S, Q.Sdf, (long long)G * G, st);
     if (ph.L1 == 0) twiddles<V>(ph.L, Q.tw, st);
     else {
       twiddles<V>(ph.L1, Q.tw, st);
@@ -453,8 +465,13 @@ struct Engine : Base {
     if (coef32) convert<double, float>(coef, coef32, 2LL * G * G, st);
   }
   template <class V> void Ainv_nat(Phys<V>& Q, const V* in, V* out, int q) {
+    DstSplit tc;
+    tc.hi = Q.Shi;
+    tc.lo = Q.Slo;
+    tc.df_S = Q.Sdf;
+    tc.df_X = Q.Xdf;
     solve_A<V>(ph, q, in, Ns, out, Ns, coef, Q.S, Q.nw, scratch, st, Q.df,
-               std::is_same<V, float>::value ? coef32 : nullptr);
+               std::is_same<V, float>::value ? coef32 : nullptr, tc);
   }
   // K X, K_ell X, K_kappa X on a tree-order panel (q columns); any output may be null
   void apply(const T* X, long long ldx, int q, T* oK, T* oL, T* oKap, long long ldo) {
@@ -640,6 +657,7 @@ struct Engine : Base {
     }
     build_leaves();
     factor();
+    if (tc_status_take(st)) throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
     for (int k = 0; k < 4; ++k) theta_built[k] = theta[k];
     built = true;
   }
@@ -1224,7 +1242,7 @@ struct Engine : Base {
       } else throw Error(HODLR_EINVAL, "which");
       permute_rows<T, double>(o, N, Yo + (size_t)c0 * N, N, d_perm_plain, N, qq, 1, st);
     }
-    HODLR_CUDA(cudaStreamSynchronize(st));
+    if (tc_status_take(st)) throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
   }
   void probe(int level, int ncols, double* out) override {
     if (level < 1 || level > tau || ncols > c) throw Error(HODLR_EINVAL, "level / ncols");

@@ -33,8 +33,24 @@ struct GemmArgs {
 template <class TA, class TB, class TC, class Acc>
 void gemm(const GemmArgs& g, Scratch s, cudaStream_t st);
 // Same contraction with double-float (hi+lo FP32) accumulation on the FP32 pipes (~48 bits).
+// Operand types: double (split on load), float, or float2 (already split by df_split).
 template <class TA, class TB, class TC>
 void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st);
+// y[i] = (hi, lo) FP32 pair of x[i] (hi = x rounded to FP32, lo = x - hi rounded).
+void df_split(const double* x, float2* y, long long n, cudaStream_t st);
+
+// FP32-accurate product C (M x N, ld ldc) = A B on the tcgen05 tensor cores (3xTF32).  A is
+// given K-major: element (m, k) at A[k + m*lda] (for a symmetric matrix, its plain storage),
+// as a TF32 head Ahi and an FP32 remainder Alo (see tf32_split); B is K x N column-major
+// (ldb).  Returns false (nothing launched) when the shape or alignment is not supported.
+bool tf32x3_gemm(const float* Ahi, const float* Alo, long long lda, const float* B, long long ldb, float* C,
+                 long long ldc, int M, int N, int K, cudaStream_t st);
+bool tf32x3_supported(int M, int K, long long lda, long long ldb, long long ldc);
+// hi = x with the low 13 mantissa bits cleared, lo = x - hi (exact); hi may alias x.
+void tf32_split(const float* x, float* hi, float* lo, long long n, cudaStream_t st);
+// Device status word of the tensor-core kernels (HODLR_ETIMEOUT after a wait gave up);
+// returns it (synchronising the stream) and clears it.
+int tc_status_take(cudaStream_t st);
 
 // ------------------------------------------------------------------------------ elementwise / data movement
 template <class TS, class TD> void convert(const TS* src, TD* dst, long long n, cudaStream_t st);
@@ -136,10 +152,20 @@ size_t fft_work_bytes(const PhysicsDesc& p, int ncols, int real_bytes);
 // matrix (2-D, G x G); work: Ns*ncols T (2-D).  df: DST products with double-float
 // accumulation (FP64 fields).  coef32: FP32 copy of the 2-D tables; when given, FP32 fields
 // run the Thomas recurrences in FP32 arithmetic.
+// tc: TF32 head and remainder of the FP32 DST matrix; when given (FP32 fields), the DST
+// products run on the tensor cores (tf32x3_gemm).  df_S / df_X: the DST matrix split into
+// double-float pairs and a scratch panel (G x G*ncols pairs) for the split field; when
+// given with df (FP64 fields), the double-float products read pre-split operands.
+struct DstSplit {
+  const float* hi = nullptr;
+  const float* lo = nullptr;
+  const float2* df_S = nullptr;
+  float2* df_X = nullptr;
+};
 template <class T>
 void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out, long long ldo,
              const double* coef, const T* S, T* work, Scratch s, cudaStream_t st, int df = 0,
-             const float* coef32 = nullptr);
+             const float* coef32 = nullptr, DstSplit tc = DstSplit());
 // per-theta coefficient tables of the Thomas recurrences (see physics.cu)
 void tridiag_tables(const PhysicsDesc& p, double kappa, double* coef, cudaStream_t st);
 template <class T> void dst_matrix(int G, T* S, cudaStream_t st);

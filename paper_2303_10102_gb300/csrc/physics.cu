@@ -906,7 +906,7 @@ template void dst_matrix<float>(int, float*, cudaStream_t);
 
 template <class T>
 void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out, long long ldo, const double* coef,
-             const T* S, T* work, Scratch s, cudaStream_t st, int df, const float* coef32) {
+             const T* S, T* work, Scratch s, cudaStream_t st, int df, const float* coef32, DstSplit tc) {
   if (ncols <= 0) return;
   const double scale = p.h * p.h;
   if (p.dim == 1) {
@@ -926,7 +926,19 @@ void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out
   g.C = work; g.ldc = G;
   auto dst = [&](const GemmArgs& a) {
     if constexpr (sizeof(T) == 8) {
+      if (df && tc.df_S && tc.df_X) {
+        df_split((const double*)a.B, tc.df_X, (long long)a.K * a.N, st);   // B is K x N with ld K
+        GemmArgs b = a;
+        b.A = tc.df_S;
+        b.B = tc.df_X;
+        gemm_df<float2, float2, double>(b, s, st);
+        return;
+      }
       if (df) { gemm_df<T, T, T>(a, s, st); return; }
+    } else {
+      // S is symmetric, so its column-major storage is also its K-major form
+      if (tc.hi && tf32x3_gemm(tc.hi, tc.lo, G, (const float*)a.B, a.ldb, (float*)a.C, a.ldc, a.M, a.N, a.K, st))
+        return;
     }
     gemm<T, T, T, T>(a, s, st);
   };
@@ -951,8 +963,8 @@ void solve_A(const PhysicsDesc& p, int ncols, const T* in, long long ldi, T* out
   dst(g);
 }
 template void solve_A<double>(const PhysicsDesc&, int, const double*, long long, double*, long long, const double*,
-                              const double*, double*, Scratch, cudaStream_t, int, const float*);
+                              const double*, double*, Scratch, cudaStream_t, int, const float*, DstSplit);
 template void solve_A<float>(const PhysicsDesc&, int, const float*, long long, float*, long long, const double*,
-                             const float*, float*, Scratch, cudaStream_t, int, const float*);
+                             const float*, float*, Scratch, cudaStream_t, int, const float*, DstSplit);
 
 }  // namespace hodlr

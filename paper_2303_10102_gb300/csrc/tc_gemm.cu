@@ -1,0 +1,339 @@
+// FP32-accurate dense products on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// Used for the DST-I products of the 2-D operator solve (A^{-1} = S T_y S with S the G x G
+// sine transform, Sec. 5.1 SPDE representation): C = S X with X a G x (G q) panel, the only
+// large dense contraction of the FP32 path.  Each operand is split into a TF32 head and an
+// FP32 remainder (hi = x with the low 13 mantissa bits cleared, lo = x - hi, exact), and
+//   C = S_hi X_hi + S_hi X_lo + S_lo X_hi
+// is accumulated in FP32 in tensor memory (3xTF32: the dropped S_lo X_lo term and the TF32
+// truncation of the remainders are ~2^-21 relative, the size of FP32 accumulation error).
+//
+// One CTA (4 warps) computes a 128 x 256 tile of C:
+//   * TMA (cp.async.bulk.tensor) stages 32-wide K slices of S_hi, S_lo (128 rows) and X
+//     (256 columns) into shared memory with the 128-byte swizzle, double-buffered, completion
+//     tracked by mbarrier transaction counts;
+//   * the CTA's threads split the X slice in place (hi) and into a second buffer (lo);
+//   * one thread issues 12 tcgen05.mma (4 K-steps x 3 products, M=128, N=256, K=8) into a
+//     128 x 256 FP32 accumulator in TMEM and commits them to the stage's mbarrier;
+//   * the epilogue reads TMEM with tcgen05.ld (one 32-lane slice per warp) and stores C
+//     column-major (coalesced along the rows).
+// Every mbarrier wait is bounded; a wait that gives up records HODLR_ETIMEOUT in a device
+// status word, waits (bounded) for the copies and products already issued, frees its TMEM
+// and returns.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "../../include/hodlr.h"
+#include "common.cuh"
+#include "ops.h"
+
+namespace hodlr {
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 32, TC_THREADS = 128, TC_STAGES = 2;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;                        // 16 KB
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;                        // 32 KB
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;      // 96 KB
+constexpr int TC_SMEM_BYTES = TC_STAGES * TC_STAGE_BYTES + 1024 + 128;
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr int TC_WAIT_LIMIT = 1 << 22;
+
+__device__ int g_tc_status;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Wait for the completion of the barrier phase with parity `ph`; false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph) {
+  const uint32_t addr = smem_u32(bar);
+  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(ph)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 bytes,
+// 8-row groups 1024 bytes apart (tcgen05 descriptor format, version 1).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)(16u >> 4) << 16;                  // leading byte offset (not used with this swizzle)
+  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
+                       const __grid_constant__ CUtensorMap mapB, int M, int N, int K, float* C, long long ldc) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(sm + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* done = full + TC_STAGES;
+  uint32_t* tslot = (uint32_t*)(done + TC_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // M tiles vary fastest, so the CTAs that share an X tile run together and reuse it from L2
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const int nk = (K + TC_BK - 1) / TC_BK;
+
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&done[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  // instruction descriptor: D FP32, A and B TF32, both K-major, N = 256, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                         ((uint32_t)(TC_BM >> 4) << 24);
+  auto stage_ptr = [&](int s, int which) -> float* {   // 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
+    unsigned char* b = sm + s * TC_STAGE_BYTES;
+    const int offs[4] = {0, TC_A_BYTES, 2 * TC_A_BYTES, 2 * TC_A_BYTES + TC_B_BYTES};
+    return (float*)(b + offs[which]);
+  };
+  auto issue_loads = [&](int kt) {
+    const int s = kt & 1;
+    mbar_expect_tx(&full[s], 2 * TC_A_BYTES + TC_B_BYTES);
+    tma_load_2d(stage_ptr(s, 0), &mapAhi, kt * TC_BK, m0, &full[s]);
+    tma_load_2d(stage_ptr(s, 1), &mapAlo, kt * TC_BK, m0, &full[s]);
+    tma_load_2d(stage_ptr(s, 2), &mapB, kt * TC_BK, n0, &full[s]);
+  };
+
+  bool ok = true;
+  int issued = 0, committed = 0;   // k-slices whose loads / products were issued (thread 0)
+  if (tid == 0) {
+    issue_loads(0);
+    issued = 1;
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt & 1;
+    if (tid == 0 && kt + 1 < nk) {
+      // the other stage was last read by the products of slice kt-1
+      if (kt >= 1 && !mbar_wait(&done[s ^ 1], ((kt - 1) >> 1) & 1)) ok = false;
+      if (ok) {
+        issue_loads(kt + 1);
+        issued = kt + 2;
+      }
+    }
+    if (ok && !mbar_wait(&full[s], (kt >> 1) & 1)) ok = false;
+    if (ok) {
+      float4* bh = (float4*)stage_ptr(s, 2);
+      float4* bl = (float4*)stage_ptr(s, 3);
+      for (int e = tid; e < TC_BN * TC_BK / 4; e += TC_THREADS) {
+        float4 v = bh[e], h, l;
+        h.x = tf32_head(v.x); l.x = v.x - h.x;
+        h.y = tf32_head(v.y); l.y = v.y - h.y;
+        h.z = tf32_head(v.z); l.z = v.z - h.z;
+        h.w = tf32_head(v.w); l.w = v.w - h.w;
+        bh[e] = h;
+        bl[e] = l;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t ah = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
+      const uint32_t bh = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        const uint32_t o = kk * 32;   // 8 FP32 values along K
+        mma_tf32(tmem, smem_desc(ah + o), smem_desc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(ah + o), smem_desc(bl + o), idesc, 1u);
+        mma_tf32(tmem, smem_desc(al + o), smem_desc(bh + o), idesc, 1u);
+      }
+      mma_commit(&done[s]);
+      committed = kt + 1;
+    }
+  }
+  if (ok) {
+    const int last = nk - 1;
+    ok = mbar_wait(&done[last & 1], (last >> 1) & 1);
+  }
+  ok = __syncthreads_and(ok) != 0;
+  if (ok) {
+    tc_fence_after();
+    const int row = m0 + 32 * warp + lane;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) C[(size_t)col * ldc + row] = __uint_as_float(r[j]);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    // give the copies and products already issued a bounded chance to land, then report
+    atomicExch(&g_tc_status, HODLR_ETIMEOUT);
+    for (int kt = committed - 1; kt >= 0 && kt >= committed - 2; --kt) mbar_wait(&done[kt & 1], (kt >> 1) & 1);
+    for (int kt = issued - 1; kt >= committed && kt >= 0; --kt) mbar_wait(&full[kt & 1], (kt >> 1) & 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+__global__ void tf32_split_kernel(const float* x, float* hi, float* lo, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = x[i], h = tf32_head(v);
+  hi[i] = h;
+  lo[i] = v - h;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+// 2-D FP32 tensor map over a column-major matrix: inner dimension (contiguous) `inner`,
+// outer `outer`, leading dimension `ld` elements; box `box_inner` x `box_outer`.
+bool make_map(CUtensorMap* m, const float* ptr, long long inner, long long outer, long long ld, int box_inner,
+              int box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tf32x3_supported(int M, int K, long long lda, long long ldb, long long ldc) {
+  return M >= TC_BM && K >= TC_BK && lda % 4 == 0 && ldb % 4 == 0 && ldc >= M;
+}
+
+void tf32_split(const float* x, float* hi, float* lo, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  tf32_split_kernel<<<cdiv(n, 256), 256, 0, st>>>(x, hi, lo, n);
+  check_launch("tf32_split");
+}
+
+bool tf32x3_gemm(const float* Ahi, const float* Alo, long long lda, const float* B, long long ldb, float* C,
+                 long long ldc, int M, int N, int K, cudaStream_t st) {
+  if (N <= 0) return true;
+  if (!tf32x3_supported(M, K, lda, ldb, ldc)) return false;
+  if (((uintptr_t)Ahi | (uintptr_t)Alo | (uintptr_t)B) & 15) return false;
+  CUtensorMap ma, ml, mb;
+  if (!make_map(&ma, Ahi, K, M, lda, TC_BK, TC_BM) || !make_map(&ml, Alo, K, M, lda, TC_BK, TC_BM) ||
+      !make_map(&mb, B, K, N, ldb, TC_BK, TC_BN))
+    return false;
+  static bool attr = false;
+  if (!attr) {
+    HODLR_CUDA(cudaFuncSetAttribute(tf32x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
+    attr = true;
+  }
+  dim3 grid(cdiv(M, TC_BM), cdiv(N, TC_BN));
+  if (grid.y > 65535) return false;
+  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+  tf32x3_gemm_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(ma, ml, mb, M, N, K, C, ldc);
+  check_launch("tf32x3_gemm_kernel");
+  if (prof) {
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = M; sh[1] = N; sh[2] = K; sh[3] = 1; sh[4] = 0; sh[5] = 0; sh[6] = 4;
+    }
+    ++g_prof.n;
+    g_prof.flops += 2.0 * (double)M * N * K;
+    g_prof.bytes += ((double)M * K * 2 + (double)K * N + (double)M * N) * 4.0;
+  }
+  return true;
+}
+
+int tc_status_take(cudaStream_t st) {
+  int v = 0, zero = 0;
+  HODLR_CUDA(cudaMemcpyFromSymbolAsync(&v, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  HODLR_CUDA(cudaStreamSynchronize(st));
+  if (v) HODLR_CUDA(cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+  return v;
+}
+
+}  // namespace hodlr

@@ -74,6 +74,19 @@ def test_tree_probe_and_physics(name):
         assert rel(Y, m.apply(X, w.theta, which)) < 1e-11, which
 
 
+@pytest.mark.parametrize("nvar", [1, 2])
+def test_fp32_physics_products_2d(nvar):
+    """FP32 physics products on a 128 x 128 grid, where the DST products of the operator solve
+    run on the tensor cores (3xTF32), against the FP64 oracle."""
+    w = synth.small_workload(dim=2, G=128, nvar=nvar, nu=0.5, theta=(1.0, 0.1, 8.0, 1e-4), leaf=256, cap=16, c=16)
+    h = ctx(w, "fp32")
+    m = Model(w.dim, w.G, w.nvar, w.nu)
+    X = np.random.default_rng(5).standard_normal((h.N, 24))
+    for which in PARAMS + ("K",):
+        Y = h.apply(w.theta, which, X).cpu().numpy()
+        assert rel(Y, m.apply(X, w.theta, which)) < 2e-5, which
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_fp64_construction_matches_oracle(name):
     w = SMALL[name]
