@@ -18,11 +18,21 @@ LaunchTrace g_trace;
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
-constexpr int NT = (BM / TM) * (BN / TN);  // 256 threads
+constexpr int BK = 16, NT = 256;
+// Output tile configurations (16 x 16 threads each): square, and two shapes for products with
+// a narrow side, so that a block with 16..32 rows (or columns) does not fill a 64-wide tile.
+template <int BM_, int BN_, int TM_, int TN_>
+struct Tile {
+  static constexpr int BM = BM_, BN = BN_, TM = TM_, TN = TN_;
+  static_assert((BM / TM) * (BN / TN) == NT, "tile threads");
+};
+using TileSq = Tile<64, 64, 4, 4>;
+using TileNarrowN = Tile<128, 32, 8, 2>;
+using TileNarrowM = Tile<32, 128, 2, 8>;
 
-template <class TA, class TB, class TC, class Acc>
+template <class TA, class TB, class TC, class Acc, class TL>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int nsplit, int kchunk, Acc* part) {
+  constexpr int BM = TL::BM, BN = TL::BN, TM = TL::TM, TN = TL::TN;
   __shared__ Acc As[BK][BM + 1];
   __shared__ Acc Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -52,29 +62,47 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int nsplit, int kc
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
 
-  for (int k0 = kb; k0 < ke; k0 += BK) {
-    // A tile: op(A)(i, k), i in [m0, m0+BM), k in [k0, k0+BK)
+  // the next tile is fetched into registers while the current one is multiplied
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
+  Acc ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
 #pragma unroll
-    for (int e = tid; e < BM * BK; e += NT) {
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
       int i, k;
       if (!g.tA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
-      int gi = m0 + i, gk = k0 + k;
-      Acc v = Acc(0);
-      if (gi < M && gk < ke)
-        v = (Acc)(g.tA ? A[gk + (long long)gi * g.lda] : A[gi + (long long)gk * g.lda]);
-      As[k][i] = v;
+      const int gi = m0 + i, gk = k0 + k;
+      ra[r] = (gi < M && gk < ke) ? (Acc)(g.tA ? A[gk + (long long)gi * g.lda] : A[gi + (long long)gk * g.lda])
+                                  : Acc(0);
     }
 #pragma unroll
-    for (int e = tid; e < BK * BN; e += NT) {
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * NT;
       int k, j;
       if (!g.tB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
-      int gj = n0 + j, gk = k0 + k;
-      Acc v = Acc(0);
-      if (gj < g.N && gk < ke)
-        v = (Acc)(g.tB ? B[gj + (long long)gk * g.ldb] : B[gk + (long long)gj * g.ldb]);
-      Bs[k][j] = v;
+      const int gj = n0 + j, gk = k0 + k;
+      rb[r] = (gj < g.N && gk < ke) ? (Acc)(g.tB ? B[gj + (long long)gk * g.ldb] : B[gk + (long long)gj * g.ldb])
+                                    : Acc(0);
+    }
+  };
+  if (kb < ke) fetch(kb);
+  for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * NT;
+      int i, k;
+      if (!g.tA) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
+      As[k][i] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * NT;
+      int k, j;
+      if (!g.tB) { k = e % BK; j = e / BK; } else { j = e % BN; k = e / BN; }
+      Bs[k][j] = rb[r];
     }
     __syncthreads();
+    if (k0 + BK < ke) fetch(k0 + BK);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       Acc a[TM], bb[TN];
@@ -282,14 +310,9 @@ bool gemv_narrow(const GemmArgs& g, cudaStream_t st) {
 
 bool sgemm_large(const GemmArgs& g, cudaStream_t st);
 
-template <class TA, class TB, class TC, class Acc>
-void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
-  if (g.K > 0 && gemv_narrow<TA, TB, TC, Acc>(g, st)) return;
-  if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
-                std::is_same<Acc, float>::value) {
-    if (sgemm_large(g, st)) return;
-  }
+template <class TA, class TB, class TC, class Acc, class TL>
+void gemm_tiles(const GemmArgs& g, Scratch s, cudaStream_t st) {
+  constexpr int BM = TL::BM, BN = TL::BN;
   int tiles = cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
   int nsplit = 1;
   if (g.K >= 512 && tiles < 4 * 152) {
@@ -309,7 +332,7 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (grid.z > 65535) throw Error(-1, "gemm: batch too large");
   const bool prof = g_prof.on && g_prof.n < g_prof.cap;
   if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
-  gemm_kernel<TA, TB, TC, Acc><<<grid, NT, 0, st>>>(g, nsplit, kchunk, (Acc*)s.ptr);
+  gemm_kernel<TA, TB, TC, Acc, TL><<<grid, NT, 0, st>>>(g, nsplit, kchunk, (Acc*)s.ptr);
   check_launch("gemm_kernel");
   if (prof) {
     cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
@@ -329,6 +352,33 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
     splitk_reduce<TC, Acc><<<rg, 256, 0, st>>>(g, nsplit, (const Acc*)s.ptr);
     check_launch("splitk_reduce");
   }
+}
+
+// tile choice: a side of at most 32 gets the matching narrow tile
+template <class F>
+void with_tile(const GemmArgs& g, F&& f) {
+  if (g.M <= 32 && g.N > 32) f(TileNarrowM());
+  else if (g.N <= 32 && g.M > 32) f(TileNarrowN());
+  else f(TileSq());
+}
+
+void splitk_reduce_f32(const GemmArgs& g, int nsplit, const float* part, cudaStream_t st) {
+  long long mn = (long long)g.M * g.N;
+  dim3 rg(cdiv(mn, 256), g.batch);
+  splitk_reduce<float, float><<<rg, 256, 0, st>>>(g, nsplit, part);
+  check_launch("splitk_reduce");
+}
+
+template <class TA, class TB, class TC, class Acc>
+void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  if (g.K > 0 && gemv_narrow<TA, TB, TC, Acc>(g, st)) return;
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
+                std::is_same<Acc, float>::value) {
+    if (tf32x3_gemm_tn(g, s, st)) return;      // tensor cores for products with K contiguous on both sides
+    if (sgemm_large(g, st)) return;
+  }
+  with_tile(g, [&](auto tl) { gemm_tiles<TA, TB, TC, Acc, decltype(tl)>(g, s, st); });
 }
 
 template void gemm<double, double, double, double>(const GemmArgs&, Scratch, cudaStream_t);
@@ -374,8 +424,9 @@ __device__ __forceinline__ DF df_fma(DF acc, DF a, DF b) {
   return {hi, e - (hi - s)};
 }
 
-template <class TA, class TB, class TC>
+template <class TA, class TB, class TC, class TL>
 __global__ void __launch_bounds__(NT) gemm_df_kernel(GemmArgs g, int nsplit, int kchunk, double* part) {
+  constexpr int BM = TL::BM, BN = TL::BN, TM = TL::TM, TN = TL::TN;
   __shared__ DF As[BK][BM + 1];
   __shared__ DF Bs[BK][BN + 1];
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;   // tile elements per thread
@@ -492,9 +543,9 @@ __global__ void df_split_kernel(const double* x, float2* y, long long n) {
 
 }  // namespace
 
-template <class TA, class TB, class TC>
-void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+template <class TA, class TB, class TC, class TL>
+void gemm_df_tiles(const GemmArgs& g, Scratch s, cudaStream_t st) {
+  constexpr int BM = TL::BM, BN = TL::BN;
   int tiles = cdiv(g.M, BM) * cdiv(g.N, BN) * g.batch;
   int nsplit = 1;
   if (g.K >= 512 && tiles < 2 * 152) {
@@ -514,7 +565,7 @@ void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (grid.z > 65535) throw Error(-1, "gemm_df: batch too large");
   const bool prof = g_prof.on && g_prof.n < g_prof.cap;
   if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
-  gemm_df_kernel<TA, TB, TC><<<grid, NT, 0, st>>>(g, nsplit, kchunk, (double*)s.ptr);
+  gemm_df_kernel<TA, TB, TC, TL><<<grid, NT, 0, st>>>(g, nsplit, kchunk, (double*)s.ptr);
   check_launch("gemm_df_kernel");
   if (prof) {
     cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
@@ -531,6 +582,12 @@ void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st) {
     splitk_reduce<TC, double><<<rg, 256, 0, st>>>(g, nsplit, (const double*)s.ptr);
     check_launch("splitk_reduce");
   }
+}
+
+template <class TA, class TB, class TC>
+void gemm_df(const GemmArgs& g, Scratch s, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  with_tile(g, [&](auto tl) { gemm_df_tiles<TA, TB, TC, decltype(tl)>(g, s, st); });
 }
 template void gemm_df<double, double, double>(const GemmArgs&, Scratch, cudaStream_t);
 template void gemm_df<float, double, double>(const GemmArgs&, Scratch, cudaStream_t);

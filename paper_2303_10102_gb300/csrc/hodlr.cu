@@ -1666,14 +1666,22 @@ int hodlr_profile_read(hodlr_ctx* h, double* out) {
   if (!h || !h->e || !out) return HODLR_EINVAL;
   try {
     double ms = 0.0;
+    double per[5][3] = {{0}};   // per kernel family: ms, flops, launches
     for (int i = 0; i < g_prof.n; ++i) {
       HODLR_CUDA(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
       float t = 0.f;
       HODLR_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
       ms += t;
+      const int* sh = g_prof.shape + 7 * i;
+      const int v = sh[6] >= 10 ? 0 : (sh[6] >= 1 && sh[6] <= 4 ? sh[6] : 0);
+      per[v][0] += t;
+      per[v][1] += 2.0 * (double)sh[0] * sh[1] * sh[2] * sh[3];
+      per[v][2] += 1.0;
     }
     out[0] = ms;
     out[1] = g_prof.n;
+    for (int v = 0; v < 5; ++v)
+      for (int k = 0; k < 3; ++k) out[4 + 3 * v + k] = per[v][k];
     // optional per-launch dump (shape and time) for kernel studies
     if (const char* path = getenv("HODLR_PROFILE_DUMP")) {
       if (FILE* f = fopen(path, "w")) {

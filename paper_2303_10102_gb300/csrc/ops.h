@@ -46,6 +46,13 @@ void df_split(const double* x, float2* y, long long n, cudaStream_t st);
 bool tf32x3_gemm(const float* Ahi, const float* Alo, long long lda, const float* B, long long ldb, float* C,
                  long long ldc, int M, int N, int K, cudaStream_t st);
 bool tf32x3_supported(int M, int K, long long lda, long long ldb, long long ldc);
+// Batched C_b = alpha A_b^T B_b + beta C_b (tA = 1, tB = 0: K contiguous in both operands) on the
+// tensor cores (3xTF32, both operands split in the kernel), split across K when the batch has
+// few tiles.  The products of a batch must be row ranges of one panel and K a multiple of 32;
+// returns false (nothing launched) otherwise.
+bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st);
+// Ordered reduction of FP32 split-K partials into C (alpha, beta, offsets as in g).
+void splitk_reduce_f32(const GemmArgs& g, int nsplit, const float* part, cudaStream_t st);
 // hi = x with the low 13 mantissa bits cleared, lo = x - hi (exact); hi may alias x.
 void tf32_split(const float* x, float* hi, float* lo, long long n, cudaStream_t st);
 // Device status word of the tensor-core kernels (HODLR_ETIMEOUT after a wait gave up);

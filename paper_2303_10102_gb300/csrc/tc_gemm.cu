@@ -114,18 +114,51 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// Problem description of one launch (every product of the batch has the same shape).
+struct TcParams {
+  int M, N, K;            // per product: C (M x N) = A (M x K, K-major) B (K x N, K-major)
+  int bn;                 // N tile: multiple of 16, at most 256
+  int nsplit, kchunk;     // split of K across CTAs (kchunk a multiple of 32)
+  long long sA, sB;       // per-product offsets along the K coordinate of the A and B maps
+  int bmap;               // B product of product b: b, b^1 or b>>1
+  int a_split;            // 1: A is split into head and remainder here; 0: the remainder has its own map
+  float alpha, beta;
+  float* C;               // nsplit == 1: C_b = C + b*sC, leading dimension ldc
+  long long ldc, sC;
+  float* part;            // nsplit > 1: partial sums, ((b*nsplit + s) * M * N) + i + j*M
+};
+
+__device__ __forceinline__ void split_tile(float* hi_io, float* lo, int n4, int tid) {
+  float4* h4 = (float4*)hi_io;
+  float4* l4 = (float4*)lo;
+  for (int e = tid; e < n4; e += TC_THREADS) {
+    float4 v = h4[e], h, l;
+    h.x = tf32_head(v.x); l.x = v.x - h.x;
+    h.y = tf32_head(v.y); l.y = v.y - h.y;
+    h.z = tf32_head(v.z); l.z = v.z - h.z;
+    h.w = tf32_head(v.w); l.w = v.w - h.w;
+    h4[e] = h;
+    l4[e] = l;
+  }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi, const __grid_constant__ CUtensorMap mapAlo,
-                       const __grid_constant__ CUtensorMap mapB, int M, int N, int K, float* C, long long ldc) {
+    tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
+                       const __grid_constant__ CUtensorMap mapB, const TcParams p) {
   extern __shared__ unsigned char tc_smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(sm + TC_STAGES * TC_STAGE_BYTES);
   uint64_t* done = full + TC_STAGES;
   uint32_t* tslot = (uint32_t*)(done + TC_STAGES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // M tiles vary fastest, so the CTAs that share an X tile run together and reuse it from L2
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  const int nk = (K + TC_BK - 1) / TC_BK;
+  // M tiles vary fastest, so the CTAs that share a B tile run together and reuse it from L2
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * p.bn;
+  const int b = blockIdx.z / p.nsplit, sp = blockIdx.z % p.nsplit;
+  const int bb = p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b);
+  const int kbeg = sp * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
+  const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
+  const long long ax0 = (long long)b * p.sA + kbeg, bx0 = (long long)bb * p.sB + kbeg;
+  const int b_bytes = p.bn * TC_BK * 4;
 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -145,25 +178,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  // instruction descriptor: D FP32, A and B TF32, both K-major, N = 256, M = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+  // instruction descriptor: D FP32, A and B TF32, both K-major, N = bn, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.bn >> 3) << 17) |
                          ((uint32_t)(TC_BM >> 4) << 24);
   auto stage_ptr = [&](int s, int which) -> float* {   // 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
-    unsigned char* b = sm + s * TC_STAGE_BYTES;
+    unsigned char* base = sm + s * TC_STAGE_BYTES;
     const int offs[4] = {0, TC_A_BYTES, 2 * TC_A_BYTES, 2 * TC_A_BYTES + TC_B_BYTES};
-    return (float*)(b + offs[which]);
+    return (float*)(base + offs[which]);
   };
   auto issue_loads = [&](int kt) {
     const int s = kt & 1;
-    mbar_expect_tx(&full[s], 2 * TC_A_BYTES + TC_B_BYTES);
-    tma_load_2d(stage_ptr(s, 0), &mapAhi, kt * TC_BK, m0, &full[s]);
-    tma_load_2d(stage_ptr(s, 1), &mapAlo, kt * TC_BK, m0, &full[s]);
-    tma_load_2d(stage_ptr(s, 2), &mapB, kt * TC_BK, n0, &full[s]);
+    mbar_expect_tx(&full[s], TC_A_BYTES * (p.a_split ? 1 : 2) + b_bytes);
+    tma_load_2d(stage_ptr(s, 0), &mapA, (int)(ax0 + kt * TC_BK), m0, &full[s]);
+    if (!p.a_split) tma_load_2d(stage_ptr(s, 1), &mapAlo, (int)(ax0 + kt * TC_BK), m0, &full[s]);
+    tma_load_2d(stage_ptr(s, 2), &mapB, (int)(bx0 + kt * TC_BK), n0, &full[s]);
   };
 
   bool ok = true;
   int issued = 0, committed = 0;   // k-slices whose loads / products were issued (thread 0)
-  if (tid == 0) {
+  if (tid == 0 && nk > 0) {
     issue_loads(0);
     issued = 1;
   }
@@ -179,17 +212,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (ok && !mbar_wait(&full[s], (kt >> 1) & 1)) ok = false;
     if (ok) {
-      float4* bh = (float4*)stage_ptr(s, 2);
-      float4* bl = (float4*)stage_ptr(s, 3);
-      for (int e = tid; e < TC_BN * TC_BK / 4; e += TC_THREADS) {
-        float4 v = bh[e], h, l;
-        h.x = tf32_head(v.x); l.x = v.x - h.x;
-        h.y = tf32_head(v.y); l.y = v.y - h.y;
-        h.z = tf32_head(v.z); l.z = v.z - h.z;
-        h.w = tf32_head(v.w); l.w = v.w - h.w;
-        bh[e] = h;
-        bl[e] = l;
-      }
+      split_tile(stage_ptr(s, 2), stage_ptr(s, 3), p.bn * TC_BK / 4, tid);
+      if (p.a_split) split_tile(stage_ptr(s, 0), stage_ptr(s, 1), TC_BM * TC_BK / 4, tid);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -210,7 +234,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       committed = kt + 1;
     }
   }
-  if (ok) {
+  if (ok && nk > 0) {
     const int last = nk - 1;
     ok = mbar_wait(&done[last & 1], (last >> 1) & 1);
   }
@@ -218,14 +242,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (ok) {
     tc_fence_after();
     const int row = m0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+    const int ncols = min(p.bn, p.N - n0);
+    for (int c0 = 0; c0 < ncols; c0 += 32) {
       uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
-      if (row < M) {
+      if (nk > 0) {
+        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) r[j] = 0u;
+      }
+      if (row < p.M) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + c0 + j;
-          if (col < N) C[(size_t)col * ldc + row] = __uint_as_float(r[j]);
+          if (c0 + j >= ncols) break;
+          const float v = __uint_as_float(r[j]);
+          if (p.nsplit == 1) {
+            float* c = p.C + (size_t)b * p.sC + (size_t)col * p.ldc + row;
+            *c = p.beta != 0.0f ? p.alpha * v + p.beta * *c : p.alpha * v;
+          } else {
+            p.part[((size_t)b * p.nsplit + sp) * ((size_t)p.M * p.N) + (size_t)col * p.M + row] = v;
+          }
         }
       }
     }
@@ -295,6 +332,32 @@ void tf32_split(const float* x, float* hi, float* lo, long long n, cudaStream_t 
   check_launch("tf32_split");
 }
 
+namespace {
+void tc_launch(const CUtensorMap& ma, const CUtensorMap& ml, const CUtensorMap& mb, const TcParams& p, int batch,
+               cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    HODLR_CUDA(cudaFuncSetAttribute(tf32x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
+    attr = true;
+  }
+  dim3 grid(cdiv(p.M, TC_BM), cdiv(p.N, p.bn), batch * p.nsplit);
+  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+  tf32x3_gemm_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(ma, ml, mb, p);
+  check_launch("tf32x3_gemm_kernel");
+  if (prof) {
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = p.M; sh[1] = p.N; sh[2] = p.K; sh[3] = batch; sh[4] = 1; sh[5] = 0; sh[6] = 4;
+    }
+    ++g_prof.n;
+    g_prof.flops += 2.0 * (double)p.M * p.N * p.K * batch;
+    g_prof.bytes += ((double)p.M * p.K + (double)p.K * p.N + (double)p.M * p.N) * 4.0 * batch;
+  }
+}
+}  // namespace
+
 bool tf32x3_gemm(const float* Ahi, const float* Alo, long long lda, const float* B, long long ldb, float* C,
                  long long ldc, int M, int N, int K, cudaStream_t st) {
   if (N <= 0) return true;
@@ -304,27 +367,49 @@ bool tf32x3_gemm(const float* Ahi, const float* Alo, long long lda, const float*
   if (!make_map(&ma, Ahi, K, M, lda, TC_BK, TC_BM) || !make_map(&ml, Alo, K, M, lda, TC_BK, TC_BM) ||
       !make_map(&mb, B, K, N, ldb, TC_BK, TC_BN))
     return false;
-  static bool attr = false;
-  if (!attr) {
-    HODLR_CUDA(cudaFuncSetAttribute(tf32x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
-    attr = true;
+  if (cdiv(N, TC_BN) > 65535) return false;
+  TcParams p{};
+  p.M = M; p.N = N; p.K = K; p.bn = TC_BN; p.nsplit = 1; p.kchunk = ((K + TC_BK - 1) / TC_BK) * TC_BK;
+  p.sA = 0; p.sB = 0; p.bmap = BMAP_ID; p.a_split = 0; p.alpha = 1.0f; p.beta = 0.0f;
+  p.C = C; p.ldc = ldc; p.sC = 0; p.part = nullptr;
+  tc_launch(ma, ml, mb, p, 1, st);
+  return true;
+}
+
+bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st) {
+  // C_b = alpha A_b^T B_{map(b)} + beta C_b with A_b = A + b*sA (K x M, ld lda) and B likewise:
+  // both operands have K contiguous.  The products of a batch must be row ranges of one panel
+  // (offsets along K inside the leading dimension), K a multiple of the 32-wide slice.
+  if (!g.tA || g.tB || g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.batch <= 0) return false;
+  if (g.K < 4 * TC_BK || g.K % TC_BK || g.M > 4 * TC_BM) return false;
+  if (g.lda % 4 || g.ldb % 4 || g.sA % 4 || g.sB % 4) return false;
+  if (((uintptr_t)g.A | (uintptr_t)g.B) & 15) return false;
+  const int nbB = g.bmap == BMAP_SHR1 ? (g.batch + 1) / 2 : g.batch;
+  if ((long long)(g.batch - 1) * g.sA + g.K > g.lda || (long long)(nbB - 1) * g.sB + g.K > g.ldb) return false;
+  if (g.bmap == BMAP_XOR1 && (g.batch & 1)) return false;
+  const int bn = g.N >= TC_BN ? TC_BN : ((g.N + 15) / 16) * 16;
+  const long long tiles = (long long)cdiv(g.M, TC_BM) * cdiv(g.N, bn) * g.batch;
+  int nsplit = 1;
+  if (tiles < 152) {
+    nsplit = (int)std::min<long long>(cdiv(2 * 152, tiles), g.K / (4 * TC_BK));
+    const size_t per = (size_t)g.batch * g.M * g.N * sizeof(float);
+    nsplit = (int)std::min<size_t>(nsplit, s.bytes / per);
+    nsplit = std::max(nsplit, 1);
   }
-  dim3 grid(cdiv(M, TC_BM), cdiv(N, TC_BN));
-  if (grid.y > 65535) return false;
-  const bool prof = g_prof.on && g_prof.n < g_prof.cap;
-  if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
-  tf32x3_gemm_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, st>>>(ma, ml, mb, M, N, K, C, ldc);
-  check_launch("tf32x3_gemm_kernel");
-  if (prof) {
-    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
-    if (g_prof.shape) {
-      int* sh = g_prof.shape + 7 * g_prof.n;
-      sh[0] = M; sh[1] = N; sh[2] = K; sh[3] = 1; sh[4] = 0; sh[5] = 0; sh[6] = 4;
-    }
-    ++g_prof.n;
-    g_prof.flops += 2.0 * (double)M * N * K;
-    g_prof.bytes += ((double)M * K * 2 + (double)K * N + (double)M * N) * 4.0;
-  }
+  int kchunk = ((cdiv(g.K, nsplit) + TC_BK - 1) / TC_BK) * TC_BK;
+  nsplit = cdiv(g.K, kchunk);
+  if ((long long)g.batch * nsplit > 65535 || cdiv(g.N, bn) > 65535) return false;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, (const float*)g.A, g.lda, g.M, g.lda, TC_BK, TC_BM) ||
+      !make_map(&mb, (const float*)g.B, g.ldb, g.N, g.ldb, TC_BK, bn))
+    return false;
+  TcParams p{};
+  p.M = g.M; p.N = g.N; p.K = g.K; p.bn = bn; p.nsplit = nsplit; p.kchunk = kchunk;
+  p.sA = g.sA; p.sB = g.sB; p.bmap = g.bmap; p.a_split = 1;
+  p.alpha = (float)g.alpha; p.beta = (float)g.beta;
+  p.C = (float*)g.C; p.ldc = g.ldc; p.sC = g.sC; p.part = (float*)s.ptr;
+  tc_launch(ma, ma, mb, p, g.batch, st);
+  if (nsplit > 1) splitk_reduce_f32(g, nsplit, (const float*)s.ptr, st);
   return true;
 }
 

@@ -275,10 +275,15 @@ class Hodlr:
     def profile(self, enable):
         self._check(self.lib.hodlr_profile(self.h, int(bool(enable))))
 
+    FAMILIES = ("gemm_kernel", "sgemm_large_kernel", "gemm_df_kernel", "gemv_kernel", "tf32x3_gemm_kernel")
+
     def profile_read(self):
-        out = np.zeros(4)
+        out = np.zeros(19)
         self._check(self.lib.hodlr_profile_read(self.h, _dp(out)))
-        return {"ms": float(out[0]), "launches": int(out[1]), "flops": float(out[2]), "bytes": float(out[3])}
+        fam = {name: {"ms": float(out[4 + 3 * v]), "flops": float(out[5 + 3 * v]), "launches": int(out[6 + 3 * v])}
+               for v, name in enumerate(self.FAMILIES)}
+        return {"ms": float(out[0]), "launches": int(out[1]), "flops": float(out[2]), "bytes": float(out[3]),
+                "families": fam}
 
     def kernel_count(self, reset=False):
         v = np.zeros(1, dtype=np.int64)

@@ -72,10 +72,14 @@ WORKLOADS = {
     # 1-D bivariate co-kriging, 2^16 points x 2 variables, leaf 256, rank 32, FP32 bulk.
     # The summed truncation residual of the leaf extraction must stay below tau2: guard 1e-7.
     "C1": Workload("C1", 1, 65536, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 256, 32, 32, 0.0, "fp32", guard=1e-7),
-    # 2-D univariate 512^2 Morton, nu = 1/2, adaptive rank tol 1e-6 cap 128, leaf 256.
-    "C2": Workload("C2", 2, 512, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32"),
+    # 2-D univariate 512^2 Morton, nu = 1/2, adaptive rank tol 1e-6 cap 128, leaf 256.  The
+    # rank guard is set to the tolerance so that the stated tolerance decides the ranks.
+    "C2": Workload("C2", 2, 512, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32", guard=1e-6),
     # 2-D bivariate 1024^2 (N = 2^21), nu = 3/2, leaf 512, tol 1e-5 cap 192, BF16 sketch.
     "C4": Workload("C4", 2, 1024, 2, 1.5, (1.0, 0.05, 10.0, 1e-4), 512, 192, 200, 1e-5, "bf16"),
+    # The 1024^2 grid (n = 2^20) of C4 with C2's univariate model and HODLR settings: the
+    # largest grid whose K~ stays positive definite (C4's bivariate model at tol 1e-5 does not).
+    "C2L": Workload("C2L", 2, 1024, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32", guard=1e-6),
     # Reduced 2-D univariate workload of C2's structure (128^2 grid) used for kernel profiles.
     "S2": Workload("S2", 2, 128, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 64, 72, 1e-6, "fp32"),
 }

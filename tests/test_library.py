@@ -51,7 +51,7 @@ def test_build_targets_sm_103a_only():
     assert sum("arch=" in f for f in pbuild.FLAGS) == 1
 
 
-@pytest.mark.parametrize("name", ["C0", "C1", "C2", "C4"])
+@pytest.mark.parametrize("name", ["C0", "C1", "C2", "C2L", "C4"])
 def test_workspace_plan(so_path, name):
     w = synth.workload(name)
     lib = plib.load()
