@@ -35,7 +35,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 FFMA peak of the SIMT pipes: 152 SMs x 128 lanes x 2 flop x clock.
 SMS, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25
-DF_INSTR_PER_MAC = 15          # FP32 instructions of one double-float multiply-add (gemm.cu df_fma)
+DF_INSTR_PER_MAC = 12          # FP32 instructions of one double-float multiply-add (gemm.cu df_fma)
 TF32_PER_BF16 = 1.1 / 2.25     # nominal dense TF32 : BF16 tensor rate
 
 
@@ -141,6 +141,14 @@ def oracle_rate(w, prec, napply_per_eval, budget_s=20.0):
                        f"excludes the oracle's dense likelihood algebra)")}
 
 
+def workload_config(w, prec, world):
+    return {"workload": w.name, "N": w.N, "grid": [w.G] * w.dim, "nvar": w.nvar, "nu": w.nu,
+            "leaf": w.leaf, "rank_cap": w.cap, "probe_columns": w.c, "tol": w.tol, "guard": w.guard,
+            "precision": prec, "parallelism": f"replicas{world}",
+            "l2": "flushed between steps (256 MB write); panels exceed L2",
+            "step": "one Fisher-scoring iteration (build + factor + NLL + grad + Fisher)"}
+
+
 def run_reference(args, w, prec):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -160,7 +168,7 @@ def run_reference(args, w, prec):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "N": w.N, "grid": [w.G] * w.dim, "nvar": w.nvar},
+            "data": "synthetic", "config": workload_config(w, prec, args.gpus),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -313,11 +321,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
             "data": "synthetic (seeded circulant-embedding Matern field through the physics map)",
-            "config": {"workload": w.name, "N": w.N, "grid": [w.G] * w.dim, "nvar": w.nvar, "nu": w.nu,
-                       "leaf": w.leaf, "rank_cap": w.cap, "probe_columns": w.c, "tol": w.tol,
-                       "precision": prec, "parallelism": f"replicas{world}",
-                       "l2": "flushed between steps (256 MB write); panels exceed L2",
-                       "step": "one Fisher-scoring iteration (build + factor + NLL + grad + Fisher)"},
+            "config": workload_config(w, prec, world),
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(y_host.numel() * 8),
                     "d2h_bytes_per_step": (1 + 4 + 16) * 8},
             "gpu_launches": int(launches),

@@ -88,19 +88,23 @@ __device__ __forceinline__ void dit_bfly(C& u, C& v, C w) {
   v = csub(u, t);
   u = cadd(u, t);
 }
+// L and nl are powers of two: index arithmetic by shifts and masks.
+__device__ __forceinline__ int log2_pow2(int n) { return __ffs(n) - 1; }
+
 template <class C>
 __device__ void dif(C* x, int L, int nl, const C* tw) {
+  const int lnl = log2_pow2(nl), lL = log2_pow2(L);
   int half = L >> 1;
   for (; half >= 4; half >>= 3) {                    // stages half, half/2, half/4
-    const int q4 = half >> 2;
+    const int q4 = half >> 2, lq4 = log2_pow2(q4);
     const int s1 = L / (2 * half), s2 = 2 * s1, s3 = 4 * s1;
-    for (int q = threadIdx.x; q < nl * (L >> 3); q += blockDim.x) {
-      const int v = q % nl, g = q / nl;
-      const int t = g % q4, blk = g / q4;
+    for (int q = threadIdx.x; q < (nl << (lL - 3)); q += blockDim.x) {
+      const int v = q & (nl - 1), g = q >> lnl;
+      const int t = g & (q4 - 1), blk = g >> lq4;
       const int i = blk * 2 * half + t;
       C e[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) e[j] = x[(i + j * q4) * nl + v];
+      for (int j = 0; j < 8; ++j) e[j] = x[((i + j * q4) << lnl) + v];
 #pragma unroll
       for (int j = 0; j < 4; ++j) dif_bfly(e[j], e[j + 4], tw[(t + j * q4) * s1]);
 #pragma unroll
@@ -111,36 +115,38 @@ __device__ void dif(C* x, int L, int nl, const C* tw) {
 #pragma unroll
       for (int j = 0; j < 8; j += 2) dif_bfly(e[j], e[j + 1], tw[t * s3]);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[(i + j * q4) * nl + v] = e[j];
+      for (int j = 0; j < 8; ++j) x[((i + j * q4) << lnl) + v] = e[j];
     }
     __syncthreads();
   }
   for (; half >= 1; half >>= 1) {
-    const int step = L / (2 * half);
-    for (int q = threadIdx.x; q < nl * (L >> 1); q += blockDim.x) {
-      int v = q % nl, bq = q / nl;
-      int t = bq % half, blk = bq / half;
-      int i0 = blk * 2 * half + t, i1 = i0 + half;
-      C a = x[i0 * nl + v], b = x[i1 * nl + v];
+    const int step = L / (2 * half), lh = log2_pow2(half);
+    for (int q = threadIdx.x; q < (nl << (lL - 1)); q += blockDim.x) {
+      const int v = q & (nl - 1), bq = q >> lnl;
+      const int t = bq & (half - 1), blk = bq >> lh;
+      const int i0 = blk * 2 * half + t, i1 = i0 + half;
+      C a = x[(i0 << lnl) + v], b = x[(i1 << lnl) + v];
       dif_bfly(a, b, tw[t * step]);
-      x[i0 * nl + v] = a;
-      x[i1 * nl + v] = b;
+      x[(i0 << lnl) + v] = a;
+      x[(i1 << lnl) + v] = b;
     }
     __syncthreads();
   }
 }
 template <class C>
 __device__ void dit(C* x, int L, int nl, const C* tw) {
+  const int lnl = log2_pow2(nl), lL = log2_pow2(L);
   int half = 1;
   for (; 8 * half <= L; half <<= 3) {                // stages half, 2 half, 4 half
+    const int lh = log2_pow2(half);
     const int s1 = L / (2 * half), s2 = s1 / 2, s3 = s1 / 4;
-    for (int q = threadIdx.x; q < nl * (L >> 3); q += blockDim.x) {
-      const int v = q % nl, g = q / nl;
-      const int t = g % half, blk = g / half;
+    for (int q = threadIdx.x; q < (nl << (lL - 3)); q += blockDim.x) {
+      const int v = q & (nl - 1), g = q >> lnl;
+      const int t = g & (half - 1), blk = g >> lh;
       const int i = blk * 8 * half + t;
       C e[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) e[j] = x[(i + j * half) * nl + v];
+      for (int j = 0; j < 8; ++j) e[j] = x[((i + j * half) << lnl) + v];
 #pragma unroll
       for (int j = 0; j < 8; j += 2) dit_bfly(e[j], e[j + 1], tw[t * s1]);
 #pragma unroll
@@ -151,20 +157,20 @@ __device__ void dit(C* x, int L, int nl, const C* tw) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) dit_bfly(e[j], e[j + 4], tw[(t + j * half) * s3]);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[(i + j * half) * nl + v] = e[j];
+      for (int j = 0; j < 8; ++j) x[((i + j * half) << lnl) + v] = e[j];
     }
     __syncthreads();
   }
   for (; half < L; half <<= 1) {
-    const int step = L / (2 * half);
-    for (int q = threadIdx.x; q < nl * (L >> 1); q += blockDim.x) {
-      int v = q % nl, bq = q / nl;
-      int t = bq % half, blk = bq / half;
-      int i0 = blk * 2 * half + t, i1 = i0 + half;
-      C u = x[i0 * nl + v], w = x[i1 * nl + v];
+    const int step = L / (2 * half), lh = log2_pow2(half);
+    for (int q = threadIdx.x; q < (nl << (lL - 1)); q += blockDim.x) {
+      const int v = q & (nl - 1), bq = q >> lnl;
+      const int t = bq & (half - 1), blk = bq >> lh;
+      const int i0 = blk * 2 * half + t, i1 = i0 + half;
+      C u = x[(i0 << lnl) + v], w = x[(i1 << lnl) + v];
       dit_bfly(u, w, tw[t * step]);
-      x[i0 * nl + v] = u;
-      x[i1 * nl + v] = w;
+      x[(i0 << lnl) + v] = u;
+      x[(i1 << lnl) + v] = w;
     }
     __syncthreads();
   }

@@ -8,14 +8,14 @@
 // is accumulated in FP32 in tensor memory (3xTF32: the dropped S_lo X_lo term and the TF32
 // truncation of the remainders are ~2^-21 relative, the size of FP32 accumulation error).
 //
-// One CTA (4 warps) computes a 128 x 256 tile of C:
+// One CTA (8 warps) computes a 128 x 256 tile of C:
 //   * TMA (cp.async.bulk.tensor) stages 32-wide K slices of S_hi, S_lo (128 rows) and X
 //     (256 columns) into shared memory with the 128-byte swizzle, double-buffered, completion
 //     tracked by mbarrier transaction counts;
 //   * the CTA's threads split the X slice in place (hi) and into a second buffer (lo);
 //   * one thread issues 12 tcgen05.mma (4 K-steps x 3 products, M=128, N=256, K=8) into a
 //     128 x 256 FP32 accumulator in TMEM and commits them to the stage's mbarrier;
-//   * the epilogue reads TMEM with tcgen05.ld (one 32-lane slice per warp) and stores C
+//   * the epilogue reads TMEM with tcgen05.ld (each warp its 32-lane slice, alternate column chunks) and stores C
 //     column-major (coalesced along the rows).
 // Every mbarrier wait is bounded; a wait that gives up records HODLR_ETIMEOUT in a device
 // status word, waits (bounded) for the copies and products already issued, frees its TMEM
@@ -31,7 +31,7 @@
 namespace hodlr {
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 32, TC_THREADS = 128, TC_STAGES = 2;
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 32, TC_THREADS = 256, TC_STAGES = 2;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 4;                        // 16 KB
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 4;                        // 32 KB
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;      // 96 KB
@@ -241,12 +241,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   ok = __syncthreads_and(ok) != 0;
   if (ok) {
     tc_fence_after();
-    const int row = m0 + 32 * warp + lane;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31; the two warp quartets take alternate column chunks
+    const int wq = warp & 3, wh = warp >> 2;
+    const int row = m0 + 32 * wq + lane;
     const int ncols = min(p.bn, p.N - n0);
-    for (int c0 = 0; c0 < ncols; c0 += 32) {
+    for (int c0 = 32 * wh; c0 < ncols; c0 += 64) {
       uint32_t r[32];
       if (nk > 0) {
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+        tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, r);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) r[j] = 0u;
