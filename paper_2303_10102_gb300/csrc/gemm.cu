@@ -29,6 +29,9 @@ struct Tile {
 using TileSq = Tile<64, 64, 4, 4>;
 using TileNarrowN = Tile<128, 32, 8, 2>;
 using TileNarrowM = Tile<32, 128, 2, 8>;
+// Sketch-width products (N = c = cap + oversampling, just above 128) with a short inner
+// dimension: one column tile covers all of N instead of a second, nearly empty one.
+using TileSketch = Tile<128, 144, 8, 9>;
 
 template <class TA, class TB, class TC, class Acc, class TL>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int nsplit, int kchunk, Acc* part) {
@@ -375,7 +378,7 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (g.K > 0 && gemv_narrow<TA, TB, TC, Acc>(g, st)) return;
   if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
                 std::is_same<Acc, float>::value) {
-    if (tf32x3_gemm_tn(g, s, st)) return;      // tensor cores for products with K contiguous on both sides
+    if (tf32x3_gemm_tn(g, s, st)) return;      // tensor cores, TMA-staged panels with K contiguous
     if (sgemm_large(g, st)) return;
   }
   with_tile(g, [&](auto tl) { gemm_tiles<TA, TB, TC, Acc, decltype(tl)>(g, s, st); });
@@ -410,18 +413,19 @@ __device__ __forceinline__ DF df_from(double x) {
 }
 __device__ __forceinline__ DF df_from(float x) { return {x, 0.0f}; }
 __device__ __forceinline__ DF df_from(float2 x) { return {x.x, x.y}; }   // operand already split
-// acc += a * b (double-float), error-free product of the high parts plus the cross terms
+// acc += a * b (double-float): the high parts' product is split exactly (FMA) and added to
+// acc.hi exactly (TwoSum); its rounding errors and the cross terms collect in acc.lo, which is
+// folded in once at the end (12 FP32 instructions; the collected terms are ~2^-24 |hi| each, so
+// K of them add ~K 2^-48 relative, as a per-step renormalisation would).
 __device__ __forceinline__ DF df_fma(DF acc, DF a, DF b) {
-  float p = a.hi * b.hi;
+  const float p = a.hi * b.hi;
   float pe = fmaf(a.hi, b.hi, -p);
   pe = fmaf(a.hi, b.lo, pe);
   pe = fmaf(a.lo, b.hi, pe);
-  float s = acc.hi + p;
-  float bb = s - acc.hi;
-  float e = (acc.hi - (s - bb)) + (p - bb);
-  e += acc.lo + pe;
-  float hi = s + e;
-  return {hi, e - (hi - s)};
+  const float s = acc.hi + p;
+  const float bb = s - acc.hi;
+  const float e = (acc.hi - (s - bb)) + (p - bb);
+  return {s, acc.lo + (e + pe)};
 }
 
 template <class TA, class TB, class TC, class TL>
