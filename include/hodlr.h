@@ -47,8 +47,11 @@ extern "C" {
 #define HODLR_ECUDA (-7)     /* a CUDA runtime call failed                        */
 
 #define HODLR_FP64 0         /* everything in FP64                                */
-#define HODLR_MIXED_FP32 1   /* FP32 sketch/GEMM bulk; FP64 leaf Cholesky, SMW
-                                cores, log-det and refinement of K~^{-1} y        */
+#define HODLR_MIXED_FP32 1   /* FP32 sketch and products (3xTF32 on the tcgen05
+                                tensor cores where the layout allows, FP32 FFMA
+                                otherwise); FP64-class leaf sketch of K~, leaf
+                                Cholesky, SMW cores, factorization sweeps and
+                                log-det (FP64 or double-float accumulation)      */
 
 typedef struct hodlr_ctx hodlr_ctx;
 
@@ -97,7 +100,9 @@ int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, voi
                  void* workspace, size_t workspace_bytes);
 
 /* Build K~(theta) and dK~/d theta_j (Alg. 1, Sec. 3.2.2, Alg. 2, Sec. 3.3) and
- * factorize K~ (eq. one way factor, App. C).  points must be NULL (regular grid). */
+ * factorize K~ (eq. one way factor, App. C).  points must be NULL (regular grid).
+ * HODLR_ENOTPD: a leaf or SMW-core Cholesky failed; HODLR_ETIMEOUT: a tensor-core product
+ * gave up waiting for its operands (bounded mbarrier wait); the context stays usable.  */
 int hodlr_build(hodlr_ctx* h, const double* theta, const double* points);
 
 /* NLL of eq. log-like approximated (negated): N/2 log 2pi + 1/2 log|K~| + 1/2 y^T K~^{-1} y.

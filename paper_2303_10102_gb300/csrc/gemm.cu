@@ -29,9 +29,6 @@ struct Tile {
 using TileSq = Tile<64, 64, 4, 4>;
 using TileNarrowN = Tile<128, 32, 8, 2>;
 using TileNarrowM = Tile<32, 128, 2, 8>;
-// Sketch-width products (N = c = cap + oversampling, just above 128) with a short inner
-// dimension: one column tile covers all of N instead of a second, nearly empty one.
-using TileSketch = Tile<128, 144, 8, 9>;
 
 template <class TA, class TB, class TC, class Acc, class TL>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g, int nsplit, int kchunk, Acc* part) {
@@ -379,6 +376,22 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
                 std::is_same<Acc, float>::value) {
     if (tf32x3_gemm_tn(g, s, st)) return;      // tensor cores, TMA-staged panels with K contiguous
+    // sketch-width products (N = cap + oversampling, a few columns past a multiple of 128): the
+    // large tiles take the multiple of 128 and a narrow tile the remaining columns, instead of a
+    // second column of nearly empty 128-wide tiles
+    const int rem = g.N % 128;
+    if (g.N > 128 && rem > 0 && rem <= 32 && g.offmode == 0) {
+      GemmArgs h = g;
+      h.N = g.N - rem;
+      if (sgemm_large(h, st)) {
+        GemmArgs t = g;
+        t.N = rem;
+        t.B = g.tB ? (const void*)((const float*)g.B + h.N) : (const void*)((const float*)g.B + (size_t)h.N * g.ldb);
+        t.C = (void*)((float*)g.C + (size_t)h.N * g.ldc);
+        if (!gemv_narrow<TA, TB, TC, Acc>(t, st)) gemm_tiles<TA, TB, TC, Acc, TileNarrowN>(t, s, st);
+        return;
+      }
+    }
     if (sgemm_large(g, st)) return;
   }
   with_tile(g, [&](auto tl) { gemm_tiles<TA, TB, TC, Acc, decltype(tl)>(g, s, st); });

@@ -713,7 +713,7 @@ struct Engine : Base {
     // FP64 leaf Cholesky, log-det and inverse
     potrf_lower(nleaves, nl, Afp, nl, (long long)nl * nl, nullptr, leaflog, d_status, st);
     double* Linv = LinvLeaf;
-    trtri_lower(nleaves, nl, Afp, nl, (long long)nl * nl, Linv, st);
+    leaf_trtri(Linv);
     {
       GemmArgs g;  // A^{-1} = L^{-T} L^{-1}
       g.M = nl; g.N = nl; g.K = nl;
@@ -729,6 +729,38 @@ struct Engine : Base {
       }
     }
     status_check("leaf Cholesky");
+  }
+  // L^{-1} of the leaf Cholesky factors by block recursion: the 32 x 32 diagonal blocks are
+  // inverted directly, then pairs of blocks of size s merge into 2s with
+  //   [[L11, 0], [L21, L22]]^{-1} = [[X11, 0], [-X22 L21 X11, X22]]
+  // (two batched products per pair; FP64 on the FP64 path, double-float on the mixed path).
+  void leaf_trtri(double* X) {
+    const int n = leaf;
+    const long long n2 = (long long)n * n;
+    if (n < 64 || (n & (n - 1)) != 0) {
+      trtri_lower(nleaves, n, Afp, n, n2, X, st);
+      return;
+    }
+    fill<double>(X, 0.0, nleaves * n2, st);
+    trtri_diag32(nleaves, n, Afp, n, n2, X, st);
+    double* Tm = (double*)WP;    // nleaves x (n/2)^2 products of the merge step
+    for (int s = 32; s < n; s *= 2) {
+      for (int o = 0; o < n; o += 2 * s) {
+        GemmArgs g;   // T = L21 X11
+        g.M = s; g.N = s; g.K = s;
+        g.A = Afp + (o + s) + (size_t)o * n; g.lda = n; g.sA = n2;
+        g.B = X + o + (size_t)o * n; g.ldb = n; g.sB = n2;
+        g.C = Tm; g.ldc = s; g.sC = (long long)s * s; g.batch = nleaves;
+        g64<double, double>(g);
+        GemmArgs h;   // X21 = -X22 T
+        h.M = s; h.N = s; h.K = s;
+        h.A = X + (o + s) + (size_t)(o + s) * n; h.lda = n; h.sA = n2;
+        h.B = Tm; h.ldb = s; h.sB = (long long)s * s;
+        h.C = X + (o + s) + (size_t)o * n; h.ldc = n; h.sC = n2;
+        h.alpha = -1.0; h.batch = nleaves;
+        g64<double, double>(h);
+      }
+    }
   }
   // Leaf sketch of the mixed path at FP64-class accuracy: the stacked-identity probe makes each
   // leaf entry a difference of two row sums over all leaves (eq. leaf sample), whose FP32
@@ -801,11 +833,18 @@ struct Engine : Base {
       // out[b] -= U[b] (ST^T_b)^T ; ST^T_b is the b-th q x wl block (s for c1, t for c2)
       GemmArgs k;
       k.M = m; k.N = q; k.K = wl;
-      k.A = U[l]; k.lda = N; k.sA = m;
+      // the FP64 panel in working precision (the sketch buffer Q1 is free during the traces), so
+      // that the update runs as a plain working-precision product
+      const T* Ul = (const T*)U[l];
+      if constexpr (sizeof(T) == 4) {
+        convert<double, T>(U[l], Q1, (long long)N * wl, st);
+        Ul = Q1;
+      }
+      k.A = Ul; k.lda = N; k.sA = m;
       k.B = stb; k.ldb = q; k.sB = (long long)q * wl; k.tB = 1;
       k.C = out; k.ldc = ldo; k.sC = m;
       k.alpha = -1.0; k.beta = 1.0; k.batch = nbk;
-      gemm<double, T, T, T>(k, scratch, st);
+      gemmT(k);
     }
   }
 

@@ -88,6 +88,9 @@ void potrf_lower(int nb, int n, double* A, long long ld, long long stride, const
 // Inverse of lower-triangular L_b into Linv_b (FP64).
 void trtri_lower(int nb, int n, const double* L, long long ld, long long stride, double* Linv,
                  cudaStream_t st);
+// Inverses of the 32 x 32 diagonal blocks of L_b written into the same blocks of X_b (n a
+// multiple of 32); the off-diagonal blocks of X_b are not touched.
+void trtri_diag32(int nb, int n, const double* L, long long ld, long long stride, double* X, cudaStream_t st);
 // Set D_b = diag + alpha * D_b for square n x n blocks (alpha*D + I when add_identity).
 void shift_identity(int nb, int n, double* D, long long ld, long long stride, double alpha,
                     double diag, cudaStream_t st);

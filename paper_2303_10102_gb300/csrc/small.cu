@@ -190,6 +190,127 @@ __global__ void potrf_lower_kernel(int n, double* Aall, long long ld, long long 
   }
 }
 
+// Blocked right-looking Cholesky of one matrix per CTA (no rank padding), 32-column panels:
+// the diagonal block is factored by one warp in shared memory, the rows below it are solved
+// against it (one row per thread), and the trailing matrix receives one rank-32 update from
+// the panel held in shared memory.  The global matrix is read and written once per panel
+// instead of once per column.
+constexpr int PB = 32;
+__global__ void potrf_blocked_kernel(int n, double* Aall, long long ld, long long stride, double* logdet,
+                                     int* status) {
+  extern __shared__ double pan[];        // n x (PB + 1): the panel rows below the diagonal block
+  __shared__ double D[PB][PB + 1];
+  __shared__ int s_fail;
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* A = Aall + (size_t)b * stride;
+  double ld_acc = 0.0;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int kb = 0; kb < n; kb += PB) {
+    const int nbk = min(PB, n - kb);
+    for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+      const int i = e % nbk, j = e / nbk;
+      D[i][j] = A[kb + i + (size_t)(kb + j) * ld];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int k = 0; k < nbk; ++k) {
+        const double dkk = D[k][k];
+        if (!(dkk > 0.0)) {
+          if (lane == 0) s_fail = 1;
+          break;
+        }
+        const double lkk = sqrt(dkk);
+        if (lane == 0) ld_acc += 2.0 * log(lkk);
+        __syncwarp();
+        if (lane > k && lane < nbk) D[lane][k] /= lkk;
+        if (lane == k) D[k][k] = lkk;
+        __syncwarp();
+        if (lane > k && lane < nbk)
+          for (int j = k + 1; j <= lane; ++j) D[lane][j] -= D[lane][k] * D[j][k];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+      const int i = e % nbk, j = e / nbk;
+      if (i >= j) A[kb + i + (size_t)(kb + j) * ld] = D[i][j];
+    }
+    const int r0 = kb + nbk, m = n - r0;
+    // panel rows: x D^T = a, forward substitution per row
+    for (int r = tid; r < m; r += blockDim.x) {
+      double x[PB];
+#pragma unroll
+      for (int t = 0; t < PB; ++t) x[t] = t < nbk ? A[r0 + r + (size_t)(kb + t) * ld] : 0.0;
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        if (t < nbk) {
+          double v = x[t];
+          for (int q = 0; q < t; ++q) v -= x[q] * D[t][q];
+          x[t] = v / D[t][t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        if (t < nbk) {
+          pan[(size_t)r * (PB + 1) + t] = x[t];
+          A[r0 + r + (size_t)(kb + t) * ld] = x[t];
+        }
+      }
+    }
+    __syncthreads();
+    // trailing update of the lower triangle: A22 -= P P^T
+    for (long long e = tid; e < (long long)m * m; e += blockDim.x) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      if (i < j) continue;
+      const double* pi = pan + (size_t)i * (PB + 1);
+      const double* pj = pan + (size_t)j * (PB + 1);
+      double acc = 0.0;
+#pragma unroll 8
+      for (int t = 0; t < nbk; ++t) acc += pi[t] * pj[t];
+      A[r0 + i + (size_t)(r0 + j) * ld] -= acc;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    if (i < j) A[i + (size_t)j * ld] = 0.0;
+  }
+  if (tid == 0) {
+    if (s_fail) *status = -3;
+    if (logdet) logdet[b] = s_fail ? NAN : ld_acc;
+  }
+}
+
+// Inverses of the 32 x 32 diagonal blocks of lower-triangular matrices (one warp per block,
+// lane c computes column c by forward substitution in shared memory); the rest of X is left
+// to the caller.
+__global__ void trtri_diag32_kernel(int nb, int n, const double* Lall, long long ld, long long stride,
+                                    double* Xall) {
+  __shared__ double Ls[4][32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = n / 32;
+  const long long gw = (long long)blockIdx.x * 4 + warp;   // (matrix, diagonal block)
+  const int b = (int)(gw / nblk), d = (int)(gw % nblk);
+  if (b >= nb) return;
+  const double* L = Lall + (size_t)b * stride + (size_t)d * 32 * (ld + 1);
+  double* X = Xall + (size_t)b * stride + (size_t)d * 32 * (ld + 1);
+  for (int j = 0; j < 32; ++j) Ls[warp][lane][j] = L[lane + (size_t)j * ld];
+  __syncwarp();
+  double x[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    double v = k == lane ? 1.0 : 0.0;
+#pragma unroll
+    for (int q = 0; q < k; ++q) v -= Ls[warp][k][q] * x[q];
+    x[k] = v / Ls[warp][k][k];
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) X[k + (size_t)lane * ld] = x[k];
+}
+
 __global__ void trtri_lower_kernel(int n, const double* Lall, long long ld, long long stride, double* Xall) {
   const int b = blockIdx.x;
   const double* L = Lall + (size_t)b * stride;
@@ -284,12 +405,13 @@ __global__ void trace_products_kernel(int n, const int* sizes, const T* X, long 
   if (!Yb) {
     for (int i = threadIdx.x; i < nb; i += blockDim.x) s += (double)Xb[i + (size_t)i * ldx];
   } else {
-    for (long long e = threadIdx.x; e < (long long)nb * nb; e += blockDim.x) {
-      int i = (int)(e % nb), j = (int)(e / nb);
-      // mode 0: tr(X Y) = sum_{i,j} X[i,j] Y[j,i];  mode 1: tr(X Y^T) = sum_{i,j} X[i,j] Y[i,j]
-      double yv = swapJ ? (double)Yb[i + (size_t)j * ldy] : (double)Yb[j + (size_t)i * ldy];
-      s += (double)Xb[i + (size_t)j * ldx] * yv;
-    }
+    // mode 0: tr(X Y) = sum_{i,j} X[i,j] Y[j,i];  mode 1: tr(X Y^T) = sum_{i,j} X[i,j] Y[i,j]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, nty = blockDim.x >> 5;
+    for (int j = ty; j < nb; j += nty)
+      for (int i = tx; i < nb; i += 32) {
+        const double yv = swapJ ? (double)Yb[i + (size_t)j * ldy] : (double)Yb[j + (size_t)i * ldy];
+        s += (double)Xb[i + (size_t)j * ldx] * yv;
+      }
   }
   double t = block_sum(s, red);
   if (threadIdx.x == 0) out[b] = t;
@@ -379,8 +501,23 @@ template void pivoted_cholesky<float>(int, int, int, int, const double*, double,
 void potrf_lower(int nb, int n, double* A, long long ld, long long stride, const int* rank, double* logdet,
                  int* status, cudaStream_t st) {
   if (nb <= 0 || n <= 0) return;
+  const size_t pan = (size_t)n * (PB + 1) * sizeof(double);
+  if (!rank && n >= 4 * PB && pan <= 200 * 1024) {
+    if (pan > 48 * 1024)
+      HODLR_CUDA(cudaFuncSetAttribute(potrf_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pan));
+    potrf_blocked_kernel<<<nb, 256, pan, st>>>(n, A, ld, stride, logdet, status);
+    check_launch("potrf_blocked");
+    return;
+  }
   potrf_lower_kernel<<<nb, 512, 0, st>>>(n, A, ld, stride, rank, logdet, status);
   check_launch("potrf_lower");
+}
+
+void trtri_diag32(int nb, int n, const double* L, long long ld, long long stride, double* X, cudaStream_t st) {
+  if (nb <= 0 || n <= 0) return;
+  const long long warps = (long long)(n / 32) * nb;
+  trtri_diag32_kernel<<<cdiv(warps, 4), 128, 0, st>>>(nb, n, L, ld, stride, X);
+  check_launch("trtri_diag32");
 }
 
 void trtri_lower(int nb, int n, const double* L, long long ld, long long stride, double* Linv, cudaStream_t st) {

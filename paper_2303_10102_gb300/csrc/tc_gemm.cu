@@ -337,11 +337,8 @@ void tf32_split(const float* x, float* hi, float* lo, long long n, cudaStream_t 
 namespace {
 void tc_launch(const CUtensorMap& ma, const CUtensorMap& ml, const CUtensorMap& mb, const TcParams& p, int batch,
                cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    HODLR_CUDA(cudaFuncSetAttribute(tf32x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
-    attr = true;
-  }
+  // per device and cheap: set on every launch rather than cached in a process-wide flag
+  HODLR_CUDA(cudaFuncSetAttribute(tf32x3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES));
   dim3 grid(cdiv(p.M, TC_BM), cdiv(p.N, p.bn), batch * p.nsplit);
   const bool prof = g_prof.on && g_prof.n < g_prof.cap;
   if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);

@@ -82,6 +82,9 @@ WORKLOADS = {
     "C2L": Workload("C2L", 2, 1024, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32", guard=1e-6),
     # Reduced 2-D univariate workload of C2's structure (128^2 grid) used for kernel profiles.
     "S2": Workload("S2", 2, 128, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 64, 72, 1e-6, "fp32"),
+    # 256^2 grid with C2's model and settings (a few GiB of workspace): kernel profiles of the
+    # operator-solve and peeling products at a size between S2 and C2.
+    "S3": Workload("S3", 2, 256, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 64, 72, 1e-6, "fp32", guard=1e-6),
 }
 
 

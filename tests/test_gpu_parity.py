@@ -54,6 +54,9 @@ SMALL = {
                                    c=56),
     "1d-nonpow2": synth.small_workload(dim=1, G=320, nvar=1, nu=1.5, theta=(0.8, 0.2, 3.0, 1e-2), leaf=40,
                                                  cap=6, c=9),
+    # leaves of 128: the blocked leaf Cholesky and the two-level block inversion of the factors
+    "1d-leaf128": synth.small_workload(dim=1, G=2048, nvar=1, nu=1.5, theta=(1.0, 0.1, 5.0, 1e-3), leaf=128,
+                                       cap=10, c=12),
 }
 
 
