@@ -141,6 +141,19 @@ def oracle_rate(w, prec, napply_per_eval, budget_s=20.0):
                        f"excludes the oracle's dense likelihood algebra)")}
 
 
+def aggregate(ms_local, steps, dist=None, device=None):
+    """Replicas: every rank times its own `steps` evaluations; the job's time is the maximum over
+    the ranks and its rate is all ranks' evaluations over that time.  Returns (ms_max, rate)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1000.0)
+
+
 def workload_config(w, prec, world):
     return {"workload": w.name, "N": w.N, "grid": [w.G] * w.dim, "nvar": w.nvar, "nu": w.nu,
             "leaf": w.leaf, "rank_cap": w.cap, "probe_columns": w.c, "tol": w.tol, "guard": w.guard,
@@ -265,11 +278,7 @@ def main():
     launches = h.kernel_count()
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_local = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * args.steps / (ms_max / 1000.0)
+    ms_max, value = aggregate(ms, args.steps, dist, dev)
 
     # ---------------- end-to-end: host y -> device every step, results back to host
     torch.cuda.synchronize()
@@ -285,10 +294,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e += e0.elapsed_time(e1)
-    t_e = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / (float(t_e.item()) / 1000.0)
+    _, e2e_value = aggregate(ms_e2e, args.steps, dist, dev)
 
     if rank == 0:
         pk = peaks()
