@@ -34,9 +34,12 @@ __device__ double block_sum(double v, double* red) {
 template <class TR>
 __global__ void pivoted_cholesky_kernel(int c, int cap, int w, const double* Gall, double thr_rel,
                                         int* rank, int* Jall, TR* Rinvall, int frozen, double* work,
-                                        int* status) {
+                                        int* status, int schur_in_smem) {
   extern __shared__ unsigned char sm_raw[];
-  int* piv = (int*)sm_raw;                       // c
+  // the c x c Schur complement lives in shared memory when it fits (it is updated at every
+  // pivot step), else in the global work area
+  double* As = (double*)sm_raw;
+  int* piv = (int*)(sm_raw + (schur_in_smem ? (size_t)c * c * sizeof(double) : 0));   // c
   int* done = piv + c;                           // c flags
   __shared__ double sv[32];
   __shared__ int si[32];
@@ -44,8 +47,9 @@ __global__ void pivoted_cholesky_kernel(int c, int cap, int w, const double* Gal
   __shared__ double s_d0;
   const int b = blockIdx.x;
   const double* G = Gall + (size_t)b * c * c;
-  double* A = work + (size_t)b * 2 * c * c;      // Schur complement (original indexing)
-  double* Rr = A + (size_t)c * c;                // factor rows: Rr[k*c + i] = R[k, i]
+  double* Ag = work + (size_t)b * 2 * c * c;
+  double* A = schur_in_smem ? As : Ag;           // Schur complement (original indexing)
+  double* Rr = Ag + (size_t)c * c;               // factor rows: Rr[k*c + i] = R[k, i]
   int* J = Jall + (size_t)b * c;
   TR* Rinv = Rinvall + (size_t)b * w * w;
   for (int e = threadIdx.x; e < c * c; e += blockDim.x) A[e] = G[e];
@@ -489,8 +493,15 @@ template <class TR>
 void pivoted_cholesky(int nb, int c, int cap, int w, const double* G, double thr_rel, int* rank, int* J,
                       TR* Rinv, int frozen, double* work, int* status, cudaStream_t st) {
   if (nb <= 0) return;
-  size_t sm = 2 * c * sizeof(int);
-  pivoted_cholesky_kernel<TR><<<nb, NTS, sm, st>>>(c, cap, w, G, thr_rel, rank, J, Rinv, frozen, work, status);
+  // shared memory for the Schur complement when the batch is at most one CTA per SM (the
+  // coarse levels, latency-bound); the deep levels keep many small CTAs per SM with it in L2
+  const size_t schur = (size_t)c * c * sizeof(double);
+  const int in_smem = schur + 2 * c * sizeof(int) <= 200 * 1024 && nb <= 152;
+  size_t sm = 2 * c * sizeof(int) + (in_smem ? schur : 0);
+  if (sm > 48 * 1024)
+    HODLR_CUDA(cudaFuncSetAttribute(pivoted_cholesky_kernel<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  pivoted_cholesky_kernel<TR><<<nb, NTS, sm, st>>>(c, cap, w, G, thr_rel, rank, J, Rinv, frozen, work, status,
+                                                   in_smem);
   check_launch("pivoted_cholesky");
 }
 template void pivoted_cholesky<double>(int, int, int, int, const double*, double, int*, int*, double*, int,
