@@ -144,7 +144,8 @@ struct Engine : Base {
   bool frozen = false;
   int nwide = 10, wide = 0;
   double* LinvLeaf = nullptr;
-  double* Ainv64 = nullptr;             // mixed path: FP64 leaf inverses for the factorization sweeps
+  double* Ainv64 = nullptr;             // mixed path: leaf inverses for the factorization sweeps (FP64,
+                                        // then split in place into double-float pairs)
 
   Engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t s_) {
     dim = m->dim; G = m->grid[0]; nvar = m->nvar; nu = m->nu; prec = m->precision;
@@ -726,6 +727,8 @@ struct Engine : Base {
         g.C = Ainv64;
         gemm_df<double, double, double>(g, scratch, st);
         convert<double, T>(Ainv64, Ainv, (long long)nleaves * nl * nl, st);
+        // the leaf solves read it as a double-float operand: split once, in place
+        df_split(Ainv64, (float2*)Ainv64, (long long)nleaves * nl * nl, st);
       }
     }
     status_check("leaf Cholesky");
@@ -870,10 +873,10 @@ struct Engine : Base {
     } else {
       GemmArgs g;
       g.M = leaf; g.N = q; g.K = leaf;
-      g.A = Ainv64; g.lda = leaf; g.sA = (long long)leaf * leaf;
+      g.A = (const float2*)Ainv64; g.lda = leaf; g.sA = (long long)leaf * leaf;
       g.B = in; g.ldb = ldi; g.sB = leaf;
       g.C = out; g.ldc = ldo; g.sC = leaf; g.batch = nleaves;
-      gemm_df<double, double, double>(g, scratch, st);
+      gemm_df<float2, double, double>(g, scratch, st);
     }
   }
   // Woodbury correction of level l on q columns (in place): within each node v of level l,
