@@ -376,6 +376,7 @@ void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
                 std::is_same<Acc, float>::value) {
     if (tf32x3_gemm_tn(g, s, st)) return;      // tensor cores, TMA-staged panels with K contiguous
+    if (tf32x3_gemm_nn(g, st)) return;         // tensor cores, M-major A and K-major B
     // sketch-width products (N = cap + oversampling, a few columns past a multiple of 128): the
     // large tiles take the multiple of 128 and a narrow tile the remaining columns, instead of a
     // second column of nearly empty 128-wide tiles

@@ -320,7 +320,7 @@ struct Engine : Base {
     qmax = std::max<size_t>(qmax, (size_t)c);
     fg = ar.take<T>((size_t)maxb * cap * qmax);
     stb = ar.take<T>((size_t)maxb * cap * qmax);
-    tpan = ar.take<T>((size_t)maxb * 2 * cap * qmax);
+    tpan = ar.take<T>((size_t)maxb * 2 * ((cap + 3) & ~3) * qmax);   // leading dimension w_l rounded up to 4
     nodeG = ar.take<T>((size_t)maxp * 4 * cap * cap * 12);
     nodeX = ar.take<T>((size_t)maxp * 4 * cap * cap * 8);
     vec_d = ar.take<double>(NN * 2);
@@ -419,21 +419,23 @@ struct Engine : Base {
       if (wl == 0 || q == 0) continue;
       int m = msize(l);
       int nbk = 1 << l;
+      // wl x q blocks with the leading dimension rounded up to 4 (16-byte rows for TMA)
+      const int wl4 = (wl + 3) & ~3;
       V* tp = (V*)tpan;
-      V* tp2 = tp + (size_t)nbk * wl * q;
+      V* tp2 = tp + (size_t)nbk * wl4 * q;
       auto tn = [&](const T* Fp, V* C) {   // C_b = F[b]^T X[b]  (wl x q per child block)
         GemmArgs g;
         g.M = wl; g.N = q; g.K = m;
         g.A = Fp; g.lda = N; g.sA = m; g.tA = 1;
         g.B = X; g.ldb = ldx; g.sB = m;
-        g.C = C; g.ldc = wl; g.sC = (long long)wl * q; g.batch = nbk;
+        g.C = C; g.ldc = wl4; g.sC = (long long)wl4 * q; g.batch = nbk;
         fgemm<V>(g);
       };
       auto nn = [&](const T* Fp, const V* Bp) {   // out[b] += sign F[b] C_{b^1}
         GemmArgs g;
         g.M = m; g.N = q; g.K = wl;
         g.A = Fp; g.lda = N; g.sA = m;
-        g.B = Bp; g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
+        g.B = Bp; g.ldb = wl4; g.sB = (long long)wl4 * q; g.bmap = BMAP_XOR1;
         g.C = out; g.ldc = ldo; g.sC = m;
         g.alpha = sign; g.beta = 1.0; g.batch = nbk;
         fgemm<V>(g);
@@ -1013,20 +1015,21 @@ struct Engine : Base {
       int wl = w[l];
       if (wl == 0) continue;
       int m = msize(l), nbk = 1 << l;
+      const int wl4 = (wl + 3) & ~3;
       V* tp = (V*)tpan;
       auto tn = [&](const T* Fp, V* C) {
         GemmArgs g;
         g.M = wl; g.N = q; g.K = m;
         g.A = Fp; g.lda = N; g.sA = m; g.tA = 1;
         g.B = X; g.ldb = ldx; g.sB = m;
-        g.C = C; g.ldc = wl; g.sC = (long long)wl * q; g.batch = nbk;
+        g.C = C; g.ldc = wl4; g.sC = (long long)wl4 * q; g.batch = nbk;
         gemm<T, V, V, V>(g, scratch, st);
       };
       auto nn = [&](const T* Fp, const V* Bp) {
         GemmArgs g;
         g.M = m; g.N = q; g.K = wl;
         g.A = Fp; g.lda = N; g.sA = m;
-        g.B = Bp; g.ldb = wl; g.sB = (long long)wl * q; g.bmap = BMAP_XOR1;
+        g.B = Bp; g.ldb = wl4; g.sB = (long long)wl4 * q; g.bmap = BMAP_XOR1;
         g.C = out; g.ldc = ldo; g.sC = m;
         g.beta = 1.0; g.batch = nbk;
         gemm<T, V, V, V>(g, scratch, st);
@@ -1035,7 +1038,7 @@ struct Engine : Base {
         tn(F[l], tp);
         nn(F[l], tp);
       } else {
-        V* tp2 = tp + (size_t)nbk * wl * q;
+        V* tp2 = tp + (size_t)nbk * wl4 * q;
         tn(F[l], tp);
         tn(dF[j][l], tp2);
         nn(dF[j][l], tp);

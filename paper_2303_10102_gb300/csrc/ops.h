@@ -51,6 +51,11 @@ bool tf32x3_supported(int M, int K, long long lda, long long ldb, long long ldc)
 // few tiles.  The products of a batch must be row ranges of one panel and K a multiple of 32;
 // returns false (nothing launched) otherwise.
 bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st);
+// Batched C_b = alpha A_b B_{map(b)} + beta C_b (tA = tB = 0: A M-contiguous, B K-contiguous) on
+// the tensor cores (3xTF32), without a split of K: A_b row ranges of one panel or stacked
+// matrices, B_b likewise (a stacked or single B when K is not a multiple of 32).  M >= 128,
+// leading dimensions multiples of 4.  Returns false (nothing launched) when not supported.
+bool tf32x3_gemm_nn(const GemmArgs& g, cudaStream_t st);
 // Ordered reduction of FP32 split-K partials into C (alpha, beta, offsets as in g).
 void splitk_reduce_f32(const GemmArgs& g, int nsplit, const float* part, cudaStream_t st);
 // hi = x with the low 13 mantissa bits cleared, lo = x - hi (exact); hi may alias x.

@@ -116,12 +116,15 @@ __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__f
 
 // Problem description of one launch (every product of the batch has the same shape).
 struct TcParams {
-  int M, N, K;            // per product: C (M x N) = A (M x K, K-major) B (K x N, K-major)
+  int M, N, K;            // per product: C (M x N) = A (M x K) B (K x N), B K-major
   int bn;                 // N tile: multiple of 16, at most 256
   int nsplit, kchunk;     // split of K across CTAs (kchunk a multiple of 32)
-  long long sA, sB;       // per-product offsets along the K coordinate of the A and B maps
+  // per-product offsets of the operand maps: along the inner (contiguous) coordinate for
+  // products that are row ranges of one panel, along the outer coordinate for stacked matrices
+  long long sA_in, sA_out, sB_in, sB_out;
   int bmap;               // B product of product b: b, b^1 or b>>1
   int a_split;            // 1: A is split into head and remainder here; 0: the remainder has its own map
+  int a_mn;               // 1: A is M-major (M contiguous): four 32-row boxes per slice, transposed in shared memory
   float alpha, beta;
   float* C;               // nsplit == 1: C_b = C + b*sC, leading dimension ldc
   long long ldc, sC;
@@ -142,6 +145,41 @@ __device__ __forceinline__ void split_tile(float* hi_io, float* lo, int n4, int 
   }
 }
 
+// M-major A slice: TMA leaves four boxes of 32 rows (128 B of M) x 32 K values, 4 KB apart,
+// each with the 128-byte swizzle (16-byte chunk index XOR K row mod 8).  Each thread gathers
+// four (m, 4 consecutive k) quads into registers ...
+__device__ __forceinline__ void gather_mn(const float* box, float4 (&q)[4], int tid) {
+  const unsigned char* bs = (const unsigned char*)box;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int e = tid + TC_THREADS * j, m = e & (TC_BM - 1), kq = e >> 7;
+    const int i = m >> 5, mc = (m & 31) >> 2, mo = (m & 3) * 4;
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = 4 * kq + t;
+      v[t] = *(const float*)(bs + i * 4096 + k * 128 + ((mc ^ (k & 7)) << 4) + mo);
+    }
+    q[j] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+// ... and, once every thread has read, stores their TF32 heads and remainders K-major (row m of
+// 128 B, chunk kq XOR m mod 8: the layout TMA gives a K-major slice).
+__device__ __forceinline__ void scatter_km(float* hi, float* lo, const float4 (&q)[4], int tid) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int e = tid + TC_THREADS * j, m = e & (TC_BM - 1), kq = e >> 7;
+    const int off = m * 128 + ((kq ^ (m & 7)) << 4);
+    float4 h, l;
+    h.x = tf32_head(q[j].x); l.x = q[j].x - h.x;
+    h.y = tf32_head(q[j].y); l.y = q[j].y - h.y;
+    h.z = tf32_head(q[j].z); l.z = q[j].z - h.z;
+    h.w = tf32_head(q[j].w); l.w = q[j].w - h.w;
+    *(float4*)((unsigned char*)hi + off) = h;
+    *(float4*)((unsigned char*)lo + off) = l;
+  }
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tf32x3_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapAlo,
                        const __grid_constant__ CUtensorMap mapB, const TcParams p) {
@@ -157,7 +195,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int bb = p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b);
   const int kbeg = sp * p.kchunk, kend = min(p.K, kbeg + p.kchunk);
   const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
-  const long long ax0 = (long long)b * p.sA + kbeg, bx0 = (long long)bb * p.sB + kbeg;
+  const long long ax0 = (long long)b * p.sA_in, ay0 = (long long)b * p.sA_out;
+  const long long bx0 = (long long)bb * p.sB_in + kbeg, by0 = (long long)bb * p.sB_out + n0;
   const int b_bytes = p.bn * TC_BK * 4;
 
   if (tid == 0) {
@@ -179,8 +218,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = *tslot;
 
   // instruction descriptor: D FP32, A and B TF32, both K-major, N = bn, M = 128
-  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.bn >> 3) << 17) |
-                         ((uint32_t)(TC_BM >> 4) << 24);
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(p.bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   auto stage_ptr = [&](int s, int which) -> float* {   // 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
     unsigned char* base = sm + s * TC_STAGE_BYTES;
     const int offs[4] = {0, TC_A_BYTES, 2 * TC_A_BYTES, 2 * TC_A_BYTES + TC_B_BYTES};
@@ -189,9 +227,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   auto issue_loads = [&](int kt) {
     const int s = kt & 1;
     mbar_expect_tx(&full[s], TC_A_BYTES * (p.a_split ? 1 : 2) + b_bytes);
-    tma_load_2d(stage_ptr(s, 0), &mapA, (int)(ax0 + kt * TC_BK), m0, &full[s]);
-    if (!p.a_split) tma_load_2d(stage_ptr(s, 1), &mapAlo, (int)(ax0 + kt * TC_BK), m0, &full[s]);
-    tma_load_2d(stage_ptr(s, 2), &mapB, (int)(bx0 + kt * TC_BK), n0, &full[s]);
+    const int k0 = kbeg + kt * TC_BK;
+    if (!p.a_mn) {
+      tma_load_2d(stage_ptr(s, 0), &mapA, (int)(ax0 + k0), (int)(ay0 + m0), &full[s]);
+      if (!p.a_split) tma_load_2d(stage_ptr(s, 1), &mapAlo, (int)(ax0 + k0), (int)(ay0 + m0), &full[s]);
+    } else {
+      // M-major A: four boxes of 32 rows (128 B) x 32 K values, 4 KB apart
+#pragma unroll
+      for (int i = 0; i < TC_BM / 32; ++i)
+        tma_load_2d((unsigned char*)stage_ptr(s, 0) + i * 4096, &mapA, (int)(ax0 + m0 + 32 * i), (int)(ay0 + k0),
+                    &full[s]);
+    }
+    tma_load_2d(stage_ptr(s, 2), &mapB, (int)bx0 + kt * TC_BK, (int)by0, &full[s]);
   };
 
   bool ok = true;
@@ -211,9 +258,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     if (ok && !mbar_wait(&full[s], (kt >> 1) & 1)) ok = false;
+    if (p.a_mn) {   // uniform over the CTA: every thread reaches the barrier
+      float4 q[4];
+      if (ok) gather_mn(stage_ptr(s, 0), q, tid);
+      __syncthreads();
+      if (ok) scatter_km(stage_ptr(s, 0), stage_ptr(s, 1), q, tid);
+    }
     if (ok) {
       split_tile(stage_ptr(s, 2), stage_ptr(s, 3), p.bn * TC_BK / 4, tid);
-      if (p.a_split) split_tile(stage_ptr(s, 0), stage_ptr(s, 1), TC_BM * TC_BK / 4, tid);
+      if (p.a_split && !p.a_mn) split_tile(stage_ptr(s, 0), stage_ptr(s, 1), TC_BM * TC_BK / 4, tid);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -225,7 +278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t bh = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 8; ++kk) {
-        const uint32_t o = kk * 32;   // 8 FP32 values along K
+        const uint32_t o = kk * 32;   // 8 FP32 values along K: 32 bytes in a K-major row
         mma_tf32(tmem, smem_desc(ah + o), smem_desc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
         mma_tf32(tmem, smem_desc(ah + o), smem_desc(bl + o), idesc, 1u);
         mma_tf32(tmem, smem_desc(al + o), smem_desc(bh + o), idesc, 1u);
@@ -254,17 +307,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = 0; j < 32; ++j) r[j] = 0u;
       }
       if (row < p.M) {
+        const int nj = min(32, ncols - c0);
+        if (p.nsplit == 1) {
+          float* c = p.C + (size_t)b * p.sC + (size_t)(n0 + c0) * p.ldc + row;
+          // all loads of C before the first store: a store may alias a later load as far as the
+          // compiler knows, which would serialise 32 load latencies
+          float cv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c0 + j;
-          if (c0 + j >= ncols) break;
-          const float v = __uint_as_float(r[j]);
-          if (p.nsplit == 1) {
-            float* c = p.C + (size_t)b * p.sC + (size_t)col * p.ldc + row;
-            *c = p.beta != 0.0f ? p.alpha * v + p.beta * *c : p.alpha * v;
-          } else {
-            p.part[((size_t)b * p.nsplit + sp) * ((size_t)p.M * p.N) + (size_t)col * p.M + row] = v;
-          }
+          for (int j = 0; j < 32; ++j) cv[j] = (p.beta != 0.0f && j < nj) ? c[(size_t)j * p.ldc] : 0.0f;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nj) c[(size_t)j * p.ldc] = p.alpha * __uint_as_float(r[j]) + p.beta * cv[j];
+        } else {
+          float* part = p.part + ((size_t)b * p.nsplit + sp) * ((size_t)p.M * p.N) + (size_t)(n0 + c0) * p.M + row;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nj) part[(size_t)j * p.M] = __uint_as_float(r[j]);
         }
       }
     }
@@ -348,7 +406,7 @@ void tc_launch(const CUtensorMap& ma, const CUtensorMap& ml, const CUtensorMap& 
     cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
     if (g_prof.shape) {
       int* sh = g_prof.shape + 7 * g_prof.n;
-      sh[0] = p.M; sh[1] = p.N; sh[2] = p.K; sh[3] = batch; sh[4] = 1; sh[5] = 0; sh[6] = 4;
+      sh[0] = p.M; sh[1] = p.N; sh[2] = p.K; sh[3] = batch; sh[4] = p.a_mn ? 0 : 1; sh[5] = 0; sh[6] = 4;
     }
     ++g_prof.n;
     g_prof.flops += 2.0 * (double)p.M * p.N * p.K * batch;
@@ -369,11 +427,16 @@ bool tf32x3_gemm(const float* Ahi, const float* Alo, long long lda, const float*
   if (cdiv(N, TC_BN) > 65535) return false;
   TcParams p{};
   p.M = M; p.N = N; p.K = K; p.bn = TC_BN; p.nsplit = 1; p.kchunk = ((K + TC_BK - 1) / TC_BK) * TC_BK;
-  p.sA = 0; p.sB = 0; p.bmap = BMAP_ID; p.a_split = 0; p.alpha = 1.0f; p.beta = 0.0f;
+  p.sA_in = 0; p.sA_out = 0; p.sB_in = 0; p.sB_out = 0; p.bmap = BMAP_ID; p.a_split = 0; p.a_mn = 0;
+  p.alpha = 1.0f; p.beta = 0.0f;
   p.C = C; p.ldc = ldc; p.sC = 0; p.part = nullptr;
   tc_launch(ma, ml, mb, p, 1, st);
   return true;
 }
+
+namespace {
+int pick_bn(int N) { return N >= TC_BN ? TC_BN : ((N + 15) / 16) * 16; }
+}  // namespace
 
 bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st) {
   // C_b = alpha A_b^T B_{map(b)} + beta C_b with A_b = A + b*sA (K x M, ld lda) and B likewise:
@@ -386,7 +449,7 @@ bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st) {
   const int nbB = g.bmap == BMAP_SHR1 ? (g.batch + 1) / 2 : g.batch;
   if ((long long)(g.batch - 1) * g.sA + g.K > g.lda || (long long)(nbB - 1) * g.sB + g.K > g.ldb) return false;
   if (g.bmap == BMAP_XOR1 && (g.batch & 1)) return false;
-  const int bn = g.N >= TC_BN ? TC_BN : ((g.N + 15) / 16) * 16;
+  const int bn = pick_bn(g.N);
   const long long tiles = (long long)cdiv(g.M, TC_BM) * cdiv(g.N, bn) * g.batch;
   int nsplit = 1;
   if (tiles < 152) {
@@ -404,11 +467,68 @@ bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st) {
     return false;
   TcParams p{};
   p.M = g.M; p.N = g.N; p.K = g.K; p.bn = bn; p.nsplit = nsplit; p.kchunk = kchunk;
-  p.sA = g.sA; p.sB = g.sB; p.bmap = g.bmap; p.a_split = 1;
+  p.sA_in = g.sA; p.sA_out = 0; p.sB_in = g.sB; p.sB_out = 0;
+  p.bmap = g.bmap; p.a_split = 1; p.a_mn = 0;
   p.alpha = (float)g.alpha; p.beta = (float)g.beta;
   p.C = (float*)g.C; p.ldc = g.ldc; p.sC = g.sC; p.part = (float*)s.ptr;
   tc_launch(ma, ma, mb, p, g.batch, st);
   if (nsplit > 1) splitk_reduce_f32(g, nsplit, (const float*)s.ptr, st);
+  return true;
+}
+
+bool tf32x3_gemm_nn(const GemmArgs& g, cudaStream_t st) {
+  // C_b = alpha A_b B_{map(b)} + beta C_b with A_b (M x K, M contiguous) and B_b (K x N, K
+  // contiguous), no split of K (the inner dimension here is a rank width or a leaf size).
+  //   A_b: row ranges of one panel (A + b*sA, b*sA + M <= lda; the map's K extent is exact)
+  //        or stacked M x K matrices (sA a multiple of lda: the K tail reads the next matrix);
+  //   B_b: row ranges of one panel (the K tail would read the next rows: K a multiple of 32)
+  //        or stacked K x N matrices / a single matrix (the map's K extent is exact: the tail
+  //        reads zeros, which also cancels a stacked A's tail).
+  if (g.tA || g.tB || g.offmode != 0 || g.M < TC_BM || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
+  if (g.lda % 4 || g.ldb % 4 || g.lda < g.M || g.ldb < g.K || g.batch > 65535) return false;
+  if (((uintptr_t)g.A | (uintptr_t)g.B) & 15) return false;
+  if (g.bmap == BMAP_XOR1 && (g.batch & 1)) return false;
+  const int nbB = g.bmap == BMAP_SHR1 ? (g.batch + 1) / 2 : g.batch;
+  const int bn = pick_bn(g.N);
+  if (cdiv(g.N, bn) > 65535) return false;
+  long long a_in = 0, a_out = 0, a_inner = g.M, a_outer = g.K;
+  if (g.batch > 1 && g.sA != 0) {
+    if (g.sA % 4 == 0 && (long long)(g.batch - 1) * g.sA + g.M <= g.lda) {
+      a_in = g.sA;
+      a_inner = g.lda;
+    } else if (g.sA % g.lda == 0 && g.sA / g.lda >= g.K) {
+      a_out = g.sA / g.lda;
+      a_outer = (long long)(g.batch - 1) * a_out + g.K;
+    } else {
+      return false;
+    }
+  }
+  long long b_in = 0, b_out = 0, b_inner = g.K, b_outer = g.N;
+  bool b_exact = true;   // the map ends at K: the K tail reads zeros
+  if (nbB > 1 && g.sB != 0) {
+    if (g.sB % 4 == 0 && (long long)(nbB - 1) * g.sB + g.K <= g.ldb) {
+      b_in = g.sB;
+      b_inner = g.ldb;
+      b_exact = false;
+    } else if (g.sB % g.ldb == 0 && g.sB / g.ldb >= g.N) {
+      b_out = g.sB / g.ldb;
+      b_outer = (long long)(nbB - 1) * b_out + g.N;
+    } else {
+      return false;
+    }
+  }
+  if (g.K % TC_BK && !b_exact) return false;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, (const float*)g.A, a_inner, a_outer, g.lda, 32, TC_BK) ||
+      !make_map(&mb, (const float*)g.B, b_inner, b_outer, g.ldb, TC_BK, bn))
+    return false;
+  TcParams p{};
+  p.M = g.M; p.N = g.N; p.K = g.K; p.bn = bn; p.nsplit = 1; p.kchunk = ((g.K + TC_BK - 1) / TC_BK) * TC_BK;
+  p.sA_in = a_in; p.sA_out = a_out; p.sB_in = b_in; p.sB_out = b_out;
+  p.bmap = g.bmap; p.a_split = 1; p.a_mn = 1;
+  p.alpha = (float)g.alpha; p.beta = (float)g.beta;
+  p.C = (float*)g.C; p.ldc = g.ldc; p.sC = g.sC; p.part = nullptr;
+  tc_launch(ma, ma, mb, p, g.batch, st);
   return true;
 }
 
