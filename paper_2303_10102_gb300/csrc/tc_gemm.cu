@@ -1,22 +1,26 @@
 // FP32-accurate dense products on the 5th-generation tensor cores (tcgen05, kind::tf32).
 //
 // Used for the DST-I products of the 2-D operator solve (A^{-1} = S T_y S with S the G x G
-// sine transform, Sec. 5.1 SPDE representation): C = S X with X a G x (G q) panel, the only
-// large dense contraction of the FP32 path.  Each operand is split into a TF32 head and an
-// FP32 remainder (hi = x with the low 13 mantissa bits cleared, lo = x - hi, exact), and
-//   C = S_hi X_hi + S_hi X_lo + S_lo X_hi
-// is accumulated in FP32 in tensor memory (3xTF32: the dropped S_lo X_lo term and the TF32
+// sine transform, Sec. 5.1 SPDE representation): C = S X with X a G x (G q) panel, and for the
+// batched FP32 products of the HODLR construction and solves (Sec. 3, Alg. 1): F_l^T X with
+// K = the block height (both operands K-contiguous) and F_l T or L X with K = a rank width or
+// a leaf size (A M-contiguous).  Each operand is split into a TF32 head and an FP32 remainder
+// (hi = x with the low 13 mantissa bits cleared, lo = x - hi, exact), and
+//   C = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// is accumulated in FP32 in tensor memory (3xTF32: the dropped A_lo B_lo term and the TF32
 // truncation of the remainders are ~2^-21 relative, the size of FP32 accumulation error).
 //
-// One CTA (8 warps) computes a 128 x 256 tile of C:
-//   * TMA (cp.async.bulk.tensor) stages 32-wide K slices of S_hi, S_lo (128 rows) and X
-//     (256 columns) into shared memory with the 128-byte swizzle, double-buffered, completion
-//     tracked by mbarrier transaction counts;
-//   * the CTA's threads split the X slice in place (hi) and into a second buffer (lo);
-//   * one thread issues 12 tcgen05.mma (4 K-steps x 3 products, M=128, N=256, K=8) into a
-//     128 x 256 FP32 accumulator in TMEM and commits them to the stage's mbarrier;
-//   * the epilogue reads TMEM with tcgen05.ld (each warp its 32-lane slice, alternate column chunks) and stores C
-//     column-major (coalesced along the rows).
+// One CTA (8 warps) computes a 128 x bn tile of C (bn <= 256, a multiple of 16):
+//   * TMA (cp.async.bulk.tensor) stages 32-wide K slices of A (128 rows) and B (bn columns)
+//     into shared memory with the 128-byte swizzle, double-buffered, completion tracked by
+//     mbarrier transaction counts;
+//   * the CTA's threads split the B slice in place (hi) and into a second buffer (lo), and A
+//     likewise; an M-contiguous A slice arrives as four 32-row boxes and is transposed into the
+//     K-major layout by the same pass, so the products always read K-major operands;
+//   * one thread issues 12 tcgen05.mma (4 K-steps x 3 products, M=128, N=bn, K=8) into a
+//     128 x bn FP32 accumulator in TMEM and commits them to the stage's mbarrier;
+//   * the epilogue reads TMEM with tcgen05.ld (each warp its 32-lane slice, alternate column
+//     chunks) and stores C column-major (coalesced along the rows), or split-K partial sums.
 // Every mbarrier wait is bounded; a wait that gives up records HODLR_ETIMEOUT in a device
 // status word, waits (bounded) for the copies and products already issued, frees its TMEM
 // and returns.
