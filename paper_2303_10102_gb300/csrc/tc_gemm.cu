@@ -521,7 +521,9 @@ bool tf32x3_gemm_nn(const GemmArgs& g, cudaStream_t st) {
       return false;
     }
   }
-  if (g.K % TC_BK && !b_exact) return false;
+  // a K tail multiplies B's zeros: A's tail must be the next matrix of the batch or the map's
+  // zero fill, never gap columns between stacked matrices (possibly uninitialised, NaN x 0 = NaN)
+  if (g.K % TC_BK && (!b_exact || (a_out != 0 && a_out != g.K))) return false;
   CUtensorMap ma, mb;
   if (!make_map(&ma, (const float*)g.A, a_inner, a_outer, g.lda, 32, TC_BK) ||
       !make_map(&mb, (const float*)g.B, b_inner, b_outer, g.ldb, TC_BK, bn))
