@@ -28,6 +28,7 @@
 #include <type_traits>
 #include <string>
 #include <map>
+#include <new>
 #include <vector>
 
 #include "../../include/hodlr.h"
@@ -1542,7 +1543,8 @@ int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, voi
                  size_t workspace_bytes) {
   if (!out || !m || !o) return HODLR_EINVAL;
   *out = nullptr;
-  hodlr_ctx* h = new hodlr_ctx;
+  hodlr_ctx* h = new (std::nothrow) hodlr_ctx;
+  if (!h) return HODLR_ENOMEM;
   try {
     h->e = make_engine(m, o, (cudaStream_t)cuda_stream);
     Arena ar;
@@ -1597,15 +1599,14 @@ int hodlr_eval(hodlr_ctx* h, const double* theta, const double* y, double* nll_o
 int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, const double* const* ys, double* nll_out,
                          double* grad_out) {
   if (!hs || nb <= 0 || !thetas || !ys || !nll_out || !grad_out) return HODLR_EINVAL;
+  // results are collected first, so that a failed call leaves the outputs untouched
+  std::vector<double> v(nb), g(4 * (size_t)nb);
   for (int i = 0; i < nb; ++i) {
-    int rc = guarded(hs[i], [&] {
-      double v, g[4];
-      hs[i]->e->eval(thetas + 4 * i, ys[i], &v, g, nullptr);
-      nll_out[i] = v;
-      std::memcpy(grad_out + 4 * i, g, sizeof(g));
-    });
+    int rc = guarded(hs[i], [&] { hs[i]->e->eval(thetas + 4 * i, ys[i], &v[i], &g[4 * (size_t)i], nullptr); });
     if (rc) return rc;
   }
+  std::memcpy(nll_out, v.data(), sizeof(double) * nb);
+  std::memcpy(grad_out, g.data(), sizeof(double) * 4 * (size_t)nb);
   return HODLR_OK;
 }
 int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out) {
