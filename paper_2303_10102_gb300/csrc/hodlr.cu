@@ -1504,6 +1504,9 @@ template <class F> static int guarded(hodlr_ctx* h, F f) {
     h->err = x.what();
     cudaGetLastError();
     return x.code;
+  } catch (const std::bad_alloc& x) {
+    h->err = x.what();
+    return HODLR_ENOMEM;
   } catch (const std::exception& x) {
     h->err = x.what();
     return HODLR_EINVAL;
@@ -1705,6 +1708,9 @@ int hodlr_profile(hodlr_ctx* h, int enable) {
   } catch (const Error& x) {
     h->err = x.what();
     return x.code;
+  } catch (const std::exception& x) {   // host allocation of the event tables
+    h->err = x.what();
+    return HODLR_ENOMEM;
   }
   return HODLR_OK;
 }
