@@ -246,3 +246,21 @@ def test_full_size_tree_order_bit_exact(name):
         assert rel(P[rows, j], ref) < 1e-6
     del h
     torch.cuda.empty_cache()
+
+
+def test_full_size_physics_products_c2():
+    """Physics products K X and dK/dtheta_j X (eq. cov model) at the bench's configuration (C2:
+    512^2 grid, mixed path, FP32 fields with the tensor-core DST) on two seeded columns, against
+    the FP64 oracle.  FP32 rounding in the operator solves (Thomas recurrences along y, DST along
+    x) grows about sqrt(2) per grid doubling: measured 1.2e-5 at 128^2 and 1.7e-5 at 256^2 for
+    the kappa derivative (two solves), so about 2.5e-5 here; the bound keeps a factor 4."""
+    w = synth.workload("C2")
+    h = ctx(w, "fp32")
+    m = Model(w.dim, w.G, w.nvar, w.nu)
+    X = np.random.default_rng(11).standard_normal((h.N, 2))
+    for which in PARAMS + ("K",):
+        Y = h.apply(w.theta, which, X).cpu().numpy()
+        assert rel(Y, m.apply(X, w.theta, which)) < 1e-4, which
+    del h
+    torch.cuda.empty_cache()
+
