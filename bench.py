@@ -203,12 +203,15 @@ def main():
     ap.add_argument("--workload", default=os.environ.get("HODLR_BENCH_WORKLOAD", "C2"))
     ap.add_argument("--precision", default=None, help="fp64 or fp32 (default: the workload's)")
     ap.add_argument("--guard", type=float, default=None, help="rank guard (default: the workload's)")
+    ap.add_argument("--tol", type=float, default=None, help="rank tolerance (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
     w = synth.workload(args.workload)
     if args.guard is not None:
         w = dataclasses.replace(w, guard=args.guard)
+    if args.tol is not None:
+        w = dataclasses.replace(w, tol=args.tol)
     prec = args.precision or ("fp64" if w.precision == "fp64" else "fp32")
     if args.impl == "reference":
         return run_reference(args, w, prec)
