@@ -251,9 +251,10 @@ def test_full_size_tree_order_bit_exact(name):
 def test_full_size_physics_products_c2():
     """Physics products K X and dK/dtheta_j X (eq. cov model) at the bench's configuration (C2:
     512^2 grid, mixed path, FP32 fields with the tensor-core DST) on two seeded columns, against
-    the FP64 oracle.  FP32 rounding in the operator solves (Thomas recurrences along y, DST along
-    x) grows about sqrt(2) per grid doubling: measured 1.2e-5 at 128^2 and 1.7e-5 at 256^2 for
-    the kappa derivative (two solves), so about 2.5e-5 here; the bound keeps a factor 4."""
+    the FP64 oracle.  The FP32 rounding of the product (FFT embedding, DST products, Thomas
+    recurrences, each about 1e-6) grows about sqrt(2) per grid doubling: measured 1.2e-5 at 128^2
+    and 1.7e-5 at 256^2 for the kappa derivative (three solves), so about 2.5e-5 here; the bound
+    keeps a factor 4."""
     w = synth.workload("C2")
     h = ctx(w, "fp32")
     m = Model(w.dim, w.G, w.nvar, w.nu)
