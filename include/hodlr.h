@@ -94,6 +94,14 @@ typedef struct {
 /* Bytes of device workspace needed by a context for (m, o).  0 on bad arguments. */
 size_t hodlr_workspace_size(const hodlr_model* m, const hodlr_opts* o);
 
+/* Host-only plan of a context for (m, o): no device work, usable without a GPU.
+ *   dims_out: host, 6 values {N, tau, leaf rows, probe columns c, rank cap, leaves}
+ *             (tau = number of levels, Sec. 3.2.2; leaves = 2^tau);
+ *   perm_out: host, N values or NULL: tree position -> natural index (the KD / Morton
+ *             order of Sec. 5.2, bivariate rows interleaved per leaf), as hodlr_perm.
+ * HODLR_EINVAL for bad arguments, HODLR_ENOTIMPL for an uneven cluster tree.  */
+int hodlr_plan(const hodlr_model* m, const hodlr_opts* o, int64_t* dims_out, int64_t* perm_out);
+
 /* Create a context.  workspace: caller-owned device buffer of >= workspace_bytes
  * bytes, 256-byte aligned.  cuda_stream: a cudaStream_t (may be NULL).  */
 int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, void* cuda_stream,

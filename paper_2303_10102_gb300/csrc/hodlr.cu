@@ -28,6 +28,7 @@
 #include <type_traits>
 #include <string>
 #include <map>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -1540,6 +1541,24 @@ size_t hodlr_workspace_size(const hodlr_model* m, const hodlr_opts* o) {
   } catch (...) {
     return 0;
   }
+}
+
+int hodlr_plan(const hodlr_model* m, const hodlr_opts* o, int64_t* dims_out, int64_t* perm_out) {
+  if (!m || !o || !dims_out) return HODLR_EINVAL;
+  try {
+    // the engine's constructor builds the tree on the host and touches no device
+    std::unique_ptr<Base> b(make_engine(m, o, nullptr));
+    dims_out[0] = b->N; dims_out[1] = b->tau; dims_out[2] = b->leaf; dims_out[3] = b->c; dims_out[4] = b->cap;
+    dims_out[5] = b->nleaves;
+    if (perm_out) std::memcpy(perm_out, b->perm64.data(), sizeof(int64_t) * b->N);
+  } catch (const Error& x) {
+    return x.code;
+  } catch (const std::bad_alloc&) {
+    return HODLR_ENOMEM;
+  } catch (...) {
+    return HODLR_EINVAL;
+  }
+  return HODLR_OK;
 }
 
 int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, void* cuda_stream, void* workspace,

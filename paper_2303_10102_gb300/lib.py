@@ -42,6 +42,7 @@ _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 SIGNATURES = {
     "hodlr_workspace_size": (C.c_size_t, [C.POINTER(Model), C.POINTER(Opts)]),
+    "hodlr_plan": (C.c_int, [C.POINTER(Model), C.POINTER(Opts), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "hodlr_create": (C.c_int, [C.POINTER(_P), C.POINTER(Model), C.POINTER(Opts), _P, _P, C.c_size_t]),
     "hodlr_build": (C.c_int, [_P, _D, _D]),
     "hodlr_nll": (C.c_int, [_P, _D, _P, _D]),

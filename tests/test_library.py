@@ -70,3 +70,37 @@ def test_workspace_plan_rejects_bad_options(so_path):
     m = plib.Model(1, (ctypes.c_int * 2)(64, 1), 2, 1.5, 0)
     o = plib.Opts(15, 4, 0, 0.0, 1, 0.0)                # leaf not a multiple of nvar
     assert lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o)) == 0
+
+
+@pytest.mark.parametrize("name", ["C0", "C1", "C2", "C2L", "C4"])
+def test_tree_order_bit_exact_at_full_size(so_path, name):
+    """a1 (KD / Morton ordering and the cluster tree, Sec. 5.2 and Sec. 3.2.2): the library's host
+    plan (hodlr_plan, no device work) equals the oracle's tree bit for bit at the workloads' full
+    sizes, up to N = 2^21."""
+    from oracle.tree import Tree
+    import numpy as np
+    w = synth.workload(name)
+    lib = plib.load()
+    m = plib.Model(w.dim, (ctypes.c_int * 2)(w.G, w.G if w.dim == 2 else 1), w.nvar, w.nu, 0)
+    o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1, 0.0)
+    dims = np.zeros(6, dtype=np.int64)
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    assert lib.hodlr_plan(ctypes.byref(m), ctypes.byref(o), dims.ctypes.data_as(P64), None) == 0
+    t = Tree(w.dim, w.G, w.nvar, w.leaf)
+    assert dims[0] == t.N and dims[1] == t.tau and dims[5] == 2 ** t.tau
+    perm = np.zeros(t.N, dtype=np.int64)
+    assert lib.hodlr_plan(ctypes.byref(m), ctypes.byref(o), dims.ctypes.data_as(P64), perm.ctypes.data_as(P64)) == 0
+    assert np.array_equal(perm, np.asarray(t.perm, dtype=np.int64))
+
+
+def test_plan_rejects_uneven_trees_and_bad_models(so_path):
+    import numpy as np
+    lib = plib.load()
+    dims = np.zeros(6, dtype=np.int64)
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    # 99 points with leaves of 32 rows: the first split gives nodes of 49 and 50 points (an uneven tree)
+    m = plib.Model(1, (ctypes.c_int * 2)(99, 1), 1, 1.5, 0)
+    o = plib.Opts(32, 8, 4, 0.0, 1, 0.0)
+    assert lib.hodlr_plan(ctypes.byref(m), ctypes.byref(o), dims.ctypes.data_as(P64), None) == -6   # ENOTIMPL
+    bad = plib.Model(3, (ctypes.c_int * 2)(16, 16), 1, 1.5, 0)
+    assert lib.hodlr_plan(ctypes.byref(bad), ctypes.byref(o), dims.ctypes.data_as(P64), None) == -1   # EINVAL
