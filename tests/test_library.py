@@ -104,3 +104,25 @@ def test_plan_rejects_uneven_trees_and_bad_models(so_path):
     assert lib.hodlr_plan(ctypes.byref(m), ctypes.byref(o), dims.ctypes.data_as(P64), None) == -6   # ENOTIMPL
     bad = plib.Model(3, (ctypes.c_int * 2)(16, 16), 1, 1.5, 0)
     assert lib.hodlr_plan(ctypes.byref(bad), ctypes.byref(o), dims.ctypes.data_as(P64), None) == -1   # EINVAL
+
+
+def test_create_argument_errors_before_device_work(so_path):
+    """hodlr_create reports bad arguments without touching the device: null pointers, an unknown
+    model or precision, and a workspace that is not 256-byte aligned (all HODLR_EINVAL)."""
+    lib = plib.load()
+    h = ctypes.c_void_p()
+    m = plib.Model(1, (ctypes.c_int * 2)(256, 1), 1, 1.5, 0)
+    o = plib.Opts(32, 8, 4, 0.0, 1, 0.0)
+    assert lib.hodlr_create(None, ctypes.byref(m), ctypes.byref(o), None, ctypes.c_void_p(256), 1 << 20) == -1
+    assert lib.hodlr_create(ctypes.byref(h), None, ctypes.byref(o), None, ctypes.c_void_p(256), 1 << 20) == -1
+    for bad in (plib.Model(3, (ctypes.c_int * 2)(16, 16), 1, 1.5, 0),      # dim
+                plib.Model(1, (ctypes.c_int * 2)(256, 1), 3, 1.5, 0),      # nvar
+                plib.Model(1, (ctypes.c_int * 2)(256, 1), 1, 2.5, 0),      # nu
+                plib.Model(1, (ctypes.c_int * 2)(256, 1), 1, 1.5, 7)):     # precision
+        assert lib.hodlr_create(ctypes.byref(h), ctypes.byref(bad), ctypes.byref(o), None, ctypes.c_void_p(256),
+                                1 << 20) == -1
+        assert not h.value
+    assert lib.hodlr_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(o), None, ctypes.c_void_p(257),
+                            1 << 30) == -1
+    assert lib.hodlr_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(o), None, None, 1 << 30) == -1
+    assert not h.value
