@@ -68,6 +68,20 @@ def test_philox_known_answers():
         assert [int(o) for o in out] == v[6:10]
 
 
+def test_normal_deviates_at_known_answer_counters():
+    """Deviates worked out by hand from the published Random123 output words: a wrong shift,
+    offset or branch in the 53-bit uniforms or the Box-Muller step changes them."""
+    with open(os.path.join(GOLD, "philox_normal_kat.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        c0, c1, c2, c3, k0, k1 = (int(x, 16) for x in r[:6])
+        a, b, z = int(r[6]), int(r[7]), float(r[8])
+        assert 0 < a <= 2 ** 53 and 0 <= b < 2 ** 53
+        got = philox.normal(np.array([c0], dtype=np.uint64), c1, c2, c3, k0 + (k1 << 32))
+        assert abs(float(got[0]) - z) <= 1e-14 * max(1.0, abs(z)), (r, got)
+
+
 def test_normals_moments_and_counter_purity():
     rows = np.arange(200000, dtype=np.uint64)
     z = philox.normal(rows, 3, 2, 0, 12345)
