@@ -219,6 +219,26 @@ int hodlr_profile_read(hodlr_ctx* h, double* out);
 int hodlr_kernel_count(const hodlr_ctx* h, int64_t* out);
 int hodlr_reset_kernel_count(hodlr_ctx* h);
 
+/* Measured arithmetic peak of one pipe of the current device (the paper has no counterpart;
+ * roofline denominators of the kernels that are not HBM-bound).  which: 0 FP32 FFMA, 1 FP64
+ * DFMA (fused multiply-adds of 16 independent chains per thread on every SM), 2 tcgen05
+ * kind::tf32, 3 tcgen05 kind::f16 with BF16 operands (one CTA per SM issuing 128 x 256
+ * MMAs back to back on shared-memory operands, FP32 accumulation in TMEM).  tflops_out:
+ * host, best of three timed launches after a warm-up, in 10^12 flop/s (a multiply-add
+ * counts 2).  Runs on the legacy default stream and synchronises it; allocates nothing.
+ * HODLR_ETIMEOUT if an MMA completion wait gave up.  */
+int hodlr_peak(int which, double* tflops_out);
+
+/* Failure-detection hook (the paper has no counterpart; for tests of the bounded waits).
+ * Sets, on the current device, how many times each tensor-core CTA polls its FIRST operand
+ * barrier before giving up (polls < 0 restores the default of 2^22 polls).  A CTA whose
+ * wait gives up records HODLR_ETIMEOUT, waits with the full limit for the copies it has
+ * already issued, frees its tensor memory and returns, so the next library call that
+ * checks the status (hodlr_build, hodlr_apply) returns HODLR_ETIMEOUT and clears it; the
+ * context stays usable.  Every other wait keeps the full limit.  Not for production use:
+ * a low limit makes correct products fail.  HODLR_ECUDA if the symbol cannot be written. */
+int hodlr_debug_wait_limit(int polls);
+
 /* Allocation-free physics product (the paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory -- code running inside another
  * framework's memory pool or under a hard memory budget, or at a point where the
@@ -226,7 +246,7 @@ int hodlr_reset_kernel_count(hodlr_ctx* h);
  * (K = A^{-1} K_u A^{-1} + tau2 I on G interior points, Matern nu = 0.5 or 1.5) without a
  * context and without any workspace: X and Y are device arrays of G x ncols doubles,
  * column-major, natural order; theta is a host array of 4 doubles; cuda_stream may be
- * NULL.  Y may not alias X.
+ * NULL.  Y may not overlap X: overlapping byte ranges return HODLR_EINVAL.
  *   Limit: G <= 2048; larger grids return HODLR_EINVAL.
  *   Scratch: a fixed 160.5 KiB array in device global memory, held by every GPU that loads
  *   the library until the process exits.  The first call on a device looks its address up

@@ -1804,6 +1804,7 @@ int hodlr_reset_kernel_count(hodlr_ctx* h) {
   g_kernel_launches = 0;
   return HODLR_OK;
 }
+int hodlr_debug_wait_limit(int polls) { return tc_set_first_wait_limit(polls); }
 const char* hodlr_last_error(const hodlr_ctx* h) { return h ? h->err.c_str() : "null context"; }
 void hodlr_destroy(hodlr_ctx* h) {
   if (!h) return;

@@ -62,6 +62,13 @@ extern "C" int hodlr_apply_static(int G, double nu, const double* theta, const d
   for (int k = 0; k < 4; ++k)
     if (!(theta[k] > 0.0)) return HODLR_EINVAL;
   if (ncols == 0) return HODLR_OK;
+  {
+    // Y is written while X is still read (the nugget term tau2 X comes last): reject any
+    // overlap of the two byte ranges instead of returning a silently wrong product
+    const uintptr_t nb = (uintptr_t)G * (uintptr_t)ncols * sizeof(double);
+    const uintptr_t x0 = (uintptr_t)X, y0 = (uintptr_t)Y;
+    if (x0 < y0 + nb && y0 < x0 + nb) return HODLR_EINVAL;
+  }
   try {
     int dev = 0;
     HODLR_CUDA(cudaGetDevice(&dev));

@@ -63,6 +63,7 @@ void tf32_split(const float* x, float* hi, float* lo, long long n, cudaStream_t 
 // Device status word of the tensor-core kernels (HODLR_ETIMEOUT after a wait gave up);
 // returns it (synchronising the stream) and clears it.
 int tc_status_take(cudaStream_t st);
+int tc_set_first_wait_limit(int polls);   // < 0: restore the default
 
 // ------------------------------------------------------------------------------ elementwise / data movement
 template <class TS, class TD> void convert(const TS* src, TD* dst, long long n, cudaStream_t st);

@@ -44,6 +44,9 @@ constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr int TC_WAIT_LIMIT = 1 << 22;
 
 __device__ int g_tc_status;
+// Poll limit of each CTA's first operand wait (a test hook: set lower from the host to make
+// that wait give up; every other wait, and the drain of issued copies, keeps TC_WAIT_LIMIT).
+__device__ int g_tc_first_wait = TC_WAIT_LIMIT;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -54,9 +57,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 // Wait for the completion of the barrier phase with parity `ph`; false if the wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph, int limit = TC_WAIT_LIMIT) {
   const uint32_t addr = smem_u32(bar);
-  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         issued = kt + 2;
       }
     }
-    if (ok && !mbar_wait(&full[s], (kt >> 1) & 1)) ok = false;
+    if (ok && !mbar_wait(&full[s], (kt >> 1) & 1, kt == 0 ? g_tc_first_wait : TC_WAIT_LIMIT)) ok = false;
     if (p.a_mn) {   // uniform over the CTA: every thread reaches the barrier
       float4 q[4];
       if (ok) gather_mn(stage_ptr(s, 0), q, tid);
@@ -536,6 +539,11 @@ bool tf32x3_gemm_nn(const GemmArgs& g, cudaStream_t st) {
   p.C = (float*)g.C; p.ldc = g.ldc; p.sC = g.sC; p.part = nullptr;
   tc_launch(ma, ma, mb, p, g.batch, st);
   return true;
+}
+
+int tc_set_first_wait_limit(int polls) {
+  const int v = polls < 0 ? TC_WAIT_LIMIT : std::min(polls, TC_WAIT_LIMIT);
+  return cudaMemcpyToSymbol(g_tc_first_wait, &v, sizeof(int)) == cudaSuccess ? HODLR_OK : HODLR_ECUDA;
 }
 
 int tc_status_take(cudaStream_t st) {

@@ -68,6 +68,8 @@ SIGNATURES = {
     "hodlr_profile_read": (C.c_int, [_P, _D]),
     "hodlr_kernel_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "hodlr_reset_kernel_count": (C.c_int, [_P]),
+    "hodlr_debug_wait_limit": (C.c_int, [C.c_int]),
+    "hodlr_peak": (C.c_int, [C.c_int, _D]),
     "hodlr_apply_static": (C.c_int, [C.c_int, C.c_double, _D, _P, _P, C.c_int, _P]),
     "hodlr_last_error": (C.c_char_p, [_P]),
     "hodlr_destroy": (None, [_P]),
