@@ -47,6 +47,12 @@ def grad(K, Ks, y):
     return np.array(g)
 
 
+def trace_prod(A, B):
+    """tr(A B) = sum_ij A_ij B_ji (the definition of the trace of a product, without forming
+    A B)."""
+    return float(np.sum(A * B.T))
+
+
 def fisher(K, Ks):
     """Expected Fisher information I_ij = 1/2 tr(K^{-1} K_i K^{-1} K_j) (eq. fisher info)."""
     cf = scipy.linalg.cho_factor(K, lower=True)
@@ -55,7 +61,7 @@ def fisher(K, Ks):
     F = np.zeros((p, p))
     for i in range(p):
         for j in range(p):
-            F[i, j] = 0.5 * np.trace(W[i] @ W[j])
+            F[i, j] = 0.5 * trace_prod(W[i], W[j])
     return F
 
 
@@ -64,12 +70,31 @@ def traces(K, Ms):
     cf = scipy.linalg.cho_factor(K, lower=True)
     W = [scipy.linalg.cho_solve(cf, M) for M in Ms]
     t = np.array([np.trace(Wi) for Wi in W])
-    f = np.array([[np.trace(Wi @ Wj) for Wj in W] for Wi in W])
+    f = np.array([[trace_prod(Wi, Wj) for Wj in W] for Wi in W])
     return t, f
 
 
 def evaluate(H, y_tree, params=("sigma2", "ell", "kappa", "tau2")):
-    """NLL, gradient and Fisher of the HODLR approximation H (tree-ordered y)."""
+    """NLL, gradient and Fisher of the HODLR approximation H (tree-ordered y).
+
+    The same definitions as nll(), grad() and fisher(), with one Cholesky factorization and
+    one solve K~^{-1} K~_j per parameter shared by the gradient and the Fisher matrix."""
     K = H.densify("K")
-    Ks = [H.densify(p) for p in params]
-    return nll(K, y_tree), grad(K, Ks, y_tree), fisher(K, Ks)
+    cf = scipy.linalg.cho_factor(K, lower=True)
+    n = K.shape[0]
+    logdet_k = 2.0 * float(np.sum(np.log(np.diag(cf[0]))))
+    alpha = scipy.linalg.cho_solve(cf, y_tree)
+    f = 0.5 * n * math.log(2.0 * math.pi) + 0.5 * logdet_k + 0.5 * float(y_tree @ alpha)
+    del K
+    W, g = [], []
+    for p in params:
+        Kj = H.densify(p)
+        Wj = scipy.linalg.cho_solve(cf, Kj)
+        g.append(0.5 * np.trace(Wj) - 0.5 * float(alpha @ (Kj @ alpha)))
+        W.append(Wj)
+        del Kj
+    F = np.zeros((len(params), len(params)))
+    for i in range(len(params)):
+        for j in range(len(params)):
+            F[i, j] = 0.5 * trace_prod(W[i], W[j])
+    return f, np.array(g), F

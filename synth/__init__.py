@@ -80,6 +80,10 @@ WORKLOADS = {
     # The 1024^2 grid (n = 2^20) of C4 with C2's univariate model and HODLR settings: the
     # largest grid whose K~ stays positive definite (C4's bivariate model at tol 1e-5 does not).
     "C2L": Workload("C2L", 2, 1024, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32", guard=1e-6),
+    # C2's model and HODLR settings (cap 128, c = 136, tol = guard = 1e-6, leaf 256) on a
+    # 128^2 grid (N = 16384, tau = 6): the parity case of the benched configuration at a size
+    # where the dense FP64 oracle still finishes (its level-1 blocks are 8192 rows high).
+    "P2": Workload("P2", 2, 128, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 128, 136, 1e-6, "fp32", guard=1e-6),
     # Reduced 2-D univariate workload of C2's structure (128^2 grid) used for kernel profiles.
     "S2": Workload("S2", 2, 128, 1, 0.5, (1.0, 0.1, 8.0, 1e-4), 256, 64, 72, 1e-6, "fp32"),
     # 256^2 grid with C2's model and settings (a few GiB of workspace): kernel profiles of the
