@@ -96,10 +96,11 @@ size_t hodlr_workspace_size(const hodlr_model* m, const hodlr_opts* o);
 
 /* Host-only plan of a context for (m, o): no device work, usable without a GPU.
  *   dims_out: host, 6 values {N, tau, leaf rows, probe columns c, rank cap, leaves}
- *             (tau = number of levels, Sec. 3.2.2; leaves = 2^tau);
+ *             (tau = number of levels, Sec. 3.2.2; leaves = 2^tau; leaf rows = the largest
+ *             leaf: median splits of any N give leaves whose sizes differ by at most one);
  *   perm_out: host, N values or NULL: tree position -> natural index (the KD / Morton
  *             order of Sec. 5.2, bivariate rows interleaved per leaf), as hodlr_perm.
- * HODLR_EINVAL for bad arguments, HODLR_ENOTIMPL for an uneven cluster tree.  */
+ * HODLR_EINVAL for bad arguments.  */
 int hodlr_plan(const hodlr_model* m, const hodlr_opts* o, int64_t* dims_out, int64_t* perm_out);
 
 /* Create a context.  workspace: caller-owned device buffer of >= workspace_bytes

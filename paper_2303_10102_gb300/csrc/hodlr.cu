@@ -68,8 +68,17 @@ struct Base {
   virtual void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) = 0;
   virtual void get_pivots(int32_t* piv) const = 0;
   virtual cudaStream_t stream() const = 0;
-  int N = 0, tau = 0, leaf = 0, c = 0, cap = 0, nleaves = 0;
-  std::vector<int64_t> perm64;
+  // N: rows of the (padded) tree layout; Nr: rows of K (natural order).  An uneven cluster
+  // tree (median splits of a size that is not leaf x 2^tau) is laid out with every leaf in a
+  // slot of the largest leaf's size: the real rows of a leaf come first in its slot, the rest
+  // are padding rows, which every panel keeps at zero and K~ keeps decoupled (unit diagonal).
+  int N = 0, Nr = 0, tau = 0, leaf = 0, c = 0, cap = 0, nleaves = 0;
+  int npad = 0;                              // padding rows (N - Nr)
+  std::vector<int64_t> perm64;               // real tree position -> natural index (Nr)
+  std::vector<int> permpad;                  // tree-layout row -> natural index, -1 = padding (N)
+  std::vector<int> rowid;                    // tree-layout row -> real tree position, -1 = padding
+  std::vector<int> real2pad;                 // real tree position -> tree-layout row (Nr)
+  std::vector<int> leafreal;                 // real rows per leaf slot
   std::vector<std::vector<int>> host_rank;   // per level
   long long napply = 0;
   double logdet = 0.0;
@@ -91,9 +100,11 @@ struct Engine : Base {
   cudaStream_t stream() const override { return st; }
   // tree
   std::vector<std::vector<int>> bnd;     // per depth: node boundaries (2^d + 1)
-  int* d_perm_plain = nullptr;           // tree position -> natural index (plain)
+  int* d_perm_plain = nullptr;           // tree-layout row -> natural index (-1 = padding)
+  int* d_real2pad = nullptr;             // real tree position -> tree-layout row
+  int* d_rowid = nullptr;                // tree-layout row -> real tree position (uneven trees only)
+  int* d_leafreal = nullptr;             // real rows per leaf slot
   std::vector<unsigned char*> d_mask;    // per level (1..tau): right-child rows
-  int* d_leafb = nullptr;
   // level data
   std::vector<T*> F, CP, dF[2];
   std::vector<double*> U, CP64;        // FP64 factorization data (App. C)
@@ -159,8 +170,9 @@ struct Engine : Base {
       throw Error(HODLR_EINVAL, "bad model or options");
     if (dim == 2 && m->grid[1] != G) throw Error(HODLR_EINVAL, "2-D grids must be square");
     Ns = dim == 1 ? G : G * G;
-    N = nvar * Ns;
-    // tree (Sec. 3.2.2 index sets; KD / Morton order of Sec. 5.2)
+    Nr = nvar * Ns;
+    // tree (Sec. 3.2.2 index sets; KD / Morton order of Sec. 5.2): every node [lo, hi) of spatial
+    // positions splits at lo + (hi - lo) / 2, tau times
     int lps = leaf / nvar;
     tau = 0;
     while ((Ns + (1 << tau) - 1) / (1 << tau) > lps) ++tau;
@@ -174,17 +186,16 @@ struct Engine : Base {
       }
       sb[d].push_back(Ns);
     }
-    bnd.resize(tau + 1);
-    for (int d = 0; d <= tau; ++d)
-      for (int v : sb[d]) bnd[d].push_back(nvar * v);
     nleaves = 1 << tau;
-    this->leaf = 0;
-    for (int b = 0; b < nleaves; ++b) this->leaf = std::max(this->leaf, bnd[tau][b + 1] - bnd[tau][b]);
-    for (int d = 0; d <= tau; ++d) {
-      int m0 = bnd[d][1] - bnd[d][0];
-      for (size_t q = 0; q + 1 < bnd[d].size(); ++q)
-        if (bnd[d][q + 1] - bnd[d][q] != m0) throw Error(HODLR_ENOTIMPL, "uneven cluster trees are not built");
-    }
+    // tree layout: leaf slots of the largest leaf's size (padding rows at the end of a slot)
+    int slot = 0;
+    for (int b = 0; b < nleaves; ++b) slot = std::max(slot, sb[tau][b + 1] - sb[tau][b]);
+    this->leaf = nvar * slot;
+    N = this->leaf * nleaves;
+    npad = N - Nr;
+    bnd.assign(tau + 1, {});
+    for (int d = 0; d <= tau; ++d)
+      for (int q = 0; q <= (1 << d); ++q) bnd[d].push_back((q << (tau - d)) * this->leaf);
     // spatial order
     std::vector<int> sp(Ns);
     if (dim == 1) {
@@ -205,15 +216,25 @@ struct Engine : Base {
       std::stable_sort(key.begin(), key.end(), [](auto& a, auto& b) { return a.first < b.first; });
       for (int i = 0; i < Ns; ++i) sp[i] = key[i].second;
     }
-    perm64.resize(N);
-    if (nvar == 1) {
-      for (int i = 0; i < N; ++i) perm64[i] = sp[i];
-    } else {
+    // real tree order: within a leaf, [variable 1 of its points, variable 2 of the same points]
+    perm64.assign(Nr, 0);
+    permpad.assign(N, -1);
+    rowid.assign(N, -1);
+    real2pad.assign(Nr, 0);
+    leafreal.assign(nleaves, 0);
+    {
       int pos = 0;
       for (int b = 0; b < nleaves; ++b) {
-        int lo = sb[tau][b], hi = sb[tau][b + 1];
-        for (int i = lo; i < hi; ++i) perm64[pos++] = sp[i];
-        for (int i = lo; i < hi; ++i) perm64[pos++] = Ns + sp[i];
+        const int lo = sb[tau][b], hi = sb[tau][b + 1], s0 = b * this->leaf;
+        int k = 0;
+        for (int v = 0; v < nvar; ++v)
+          for (int i = lo; i < hi; ++i, ++k, ++pos) {
+            perm64[pos] = v * Ns + sp[i];
+            permpad[s0 + k] = (int)perm64[pos];
+            rowid[s0 + k] = pos;
+            real2pad[pos] = s0 + k;
+          }
+        leafreal[b] = k;
       }
     }
     // physics geometry
@@ -261,9 +282,11 @@ struct Engine : Base {
   void carve(Arena& ar) {
     const size_t NN = (size_t)N;
     d_perm_plain = ar.take<int>(N);
+    d_real2pad = ar.take<int>(Nr);
+    d_rowid = npad ? ar.take<int>(N) : nullptr;
+    d_leafreal = ar.take<int>(nleaves);
     d_mask.assign(tau + 1, nullptr);
     for (int l = 1; l <= tau; ++l) d_mask[l] = ar.take<unsigned char>(N);
-    d_leafb = ar.take<int>(nleaves + 1);
     F.assign(tau + 1, nullptr); U.assign(tau + 1, nullptr); CP.assign(tau + 1, nullptr); CP64.assign(tau + 1, nullptr);
     dF[0].assign(tau + 1, nullptr); dF[1].assign(tau + 1, nullptr);
     d_rank.assign(tau + 1, nullptr); d_piv.assign(tau + 1, nullptr); d_nodelog.assign(tau + 1, nullptr);
@@ -345,27 +368,27 @@ struct Engine : Base {
   }
 
   void upload_tree() {
-    std::vector<int> pp(N);
-    for (int i = 0; i < N; ++i) pp[i] = (int)perm64[i];
-    HODLR_CUDA(cudaMemcpyAsync(d_perm_plain, pp.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    HODLR_CUDA(cudaMemcpyAsync(d_perm_plain, permpad.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    HODLR_CUDA(cudaMemcpyAsync(d_real2pad, real2pad.data(), Nr * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (d_rowid) HODLR_CUDA(cudaMemcpyAsync(d_rowid, rowid.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    HODLR_CUDA(cudaMemcpyAsync(d_leafreal, leafreal.data(), nleaves * sizeof(int), cudaMemcpyHostToDevice, st));
     upload_phys(P);
     if (P64.perm) upload_phys(P64);
     for (int l = 1; l <= tau; ++l) {
       std::vector<unsigned char> m(N, 0);
       const auto& b = bnd[l];
       for (size_t q = 1; q + 1 < b.size(); q += 2)
-        for (int i = b[q]; i < b[q + 1]; ++i) m[i] = 1;
+        for (int i = b[q]; i < b[q + 1]; ++i) m[i] = rowid[i] >= 0 ? 1 : 0;
       HODLR_CUDA(cudaMemcpyAsync(d_mask[l], m.data(), N, cudaMemcpyHostToDevice, st));
       HODLR_CUDA(cudaStreamSynchronize(st));
     }
-    HODLR_CUDA(cudaMemcpyAsync(d_leafb, bnd[tau].data(), (nleaves + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
   template <class V> void upload_phys(Phys<V>& Q) {
     std::vector<int> pv(N);
     for (int i = 0; i < N; ++i) {
-      int n = (int)perm64[i];
-      pv[i] = nvar == 1 ? n : (n % Ns) + (n / Ns) * (Ns * Q.qc);
+      const int n = permpad[i];
+      pv[i] = n < 0 ? -1 : (nvar == 1 ? n : (n % Ns) + (n / Ns) * (Ns * Q.qc));
     }
     HODLR_CUDA(cudaMemcpyAsync(Q.perm, pv.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
     if (dim == 2) dst_matrix<V>(G, Q.S, st);
@@ -568,7 +591,7 @@ struct Engine : Base {
       const int np = npairs(l);
       const int m = msize(l);          // child block size
       // --- sketch of the level's blocks: Y = (K - sum_{l'<l} H^(l')) R^(l)
-      probe_panel<T>(N, c, l, 0, seed, d_mask[l], R, N, st);
+      probe_panel<T>(N, c, l, 0, seed, d_mask[l], d_rowid, R, N, st);
       apply(R, N, c, KR, KjR[0], KjR[1], N);
       HODLR_CUDA(cudaMemcpyAsync(Y, KR, sizeof(T) * (size_t)N * c, cudaMemcpyDeviceToDevice, st));
       offdiag(1, l - 1, -1, R, N, c, Y, N);
@@ -710,9 +733,9 @@ struct Engine : Base {
       offdiag(1, tau, -1, Sl, N, nl, E[0], N);
       offdiag(1, tau, 0, Sl, N, nl, E[1], N);
       offdiag(1, tau, 1, Sl, N, nl, E[2], N);
-      extract_leaves<T, double>(nleaves, nl, d_leafb, E[0], N, Afp, st);
-      extract_leaves<T, T>(nleaves, nl, d_leafb, E[1], N, dA[0], st);
-      extract_leaves<T, T>(nleaves, nl, d_leafb, E[2], N, dA[1], st);
+      extract_leaves<T, double>(nleaves, nl, d_leafreal, E[0], N, Afp, st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[1], N, dA[0], st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[2], N, dA[1], st);
     }
     convert<double, T>(Afp, A, (long long)nleaves * nl * nl, st);
     // FP64 leaf Cholesky, log-det and inverse
@@ -783,8 +806,8 @@ struct Engine : Base {
       apply(Sl, N, nl, nullptr, E[1], E[2], N);
       offdiag(1, tau, 0, Sl, N, nl, E[1], N);
       offdiag(1, tau, 1, Sl, N, nl, E[2], N);
-      extract_leaves<T, T>(nleaves, nl, d_leafb, E[1], N, dA[0], st);
-      extract_leaves<T, T>(nleaves, nl, d_leafb, E[2], N, dA[1], st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[1], N, dA[0], st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[2], N, dA[1], st);
     }
     // leaf blocks of K~ in FP64-class arithmetic, in column chunks
     const int qcl = std::max(1, std::min(64, wide / 4));
@@ -1212,8 +1235,8 @@ struct Engine : Base {
     if (nll || grad) {
       if (!y) throw Error(HODLR_EINVAL, "y is required");
       HODLR_CUDA(cudaMemsetAsync(d_status + 1, 0, sizeof(int), st));
-      check_finite<double>(y, N, d_status + 1, st);
-      permute_rows<double, double>(y, N, vec_d, N, d_perm_plain, N, 1, 0, st);   // y in tree order
+      check_finite<double>(y, Nr, d_status + 1, st);
+      permute_rows<double, double>(y, Nr, vec_d, N, d_perm_plain, N, 1, 0, st);   // y in tree order
       solve_tree(vec_d, vec_d + N);                                               // alpha
       double* alpha = vec_d + N;
       dot_columns<double, double>(N, 1, vec_d, N, alpha, N, res + 40, st);        // y^T alpha
@@ -1233,8 +1256,14 @@ struct Engine : Base {
       a_y = h[0]; a_a = h[1]; aKa[0] = h[2]; aKa[1] = h[3];
     }
     double t[3] = {0, 0, 0}, f[9] = {0};
-    if (grad || fisher) traces_impl(fisher != nullptr, t, f);
-    const double n = (double)N;
+    if (grad || fisher) {
+      traces_impl(fisher != nullptr, t, f);
+      // padding rows carry a unit diagonal decoupled from everything else: they add 1 each to
+      // tr(K~^{-1}) and tr(K~^{-2}) and nothing to any other trace
+      t[0] -= npad;
+      f[0] -= npad;
+    }
+    const double n = (double)Nr;
     double out_nll = 0.5 * n * log(2.0 * M_PI) + 0.5 * logdet + 0.5 * a_y;
     // traces of K~^{-1} K~_j: sigma2 -> (N - tau2 t0)/sigma2, ell -> t1, kappa -> t2, tau2 -> t0
     double trj[4] = {(n - t2 * t[0]) / s2, t[1], t[2], t[0]};
@@ -1276,7 +1305,7 @@ struct Engine : Base {
     // natural -> tree (T), apply, tree -> natural (double)
     for (int c0 = 0; c0 < ncols; c0 += c) {
       int qq = std::min(c, ncols - c0);
-      permute_rows<double, T>(X + (size_t)c0 * N, N, R, N, d_perm_plain, N, qq, 0, st);
+      permute_rows<double, T>(X + (size_t)c0 * Nr, Nr, R, N, d_perm_plain, N, qq, 0, st);
       T* o = KR;
       if (which == 0) apply(R, N, qq, o, nullptr, nullptr, N);
       else if (which == 2) apply(R, N, qq, nullptr, o, nullptr, N);
@@ -1287,32 +1316,34 @@ struct Engine : Base {
       } else if (which == 4) {
         HODLR_CUDA(cudaMemcpyAsync(o, R, sizeof(T) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
       } else throw Error(HODLR_EINVAL, "which");
-      permute_rows<T, double>(o, N, Yo + (size_t)c0 * N, N, d_perm_plain, N, qq, 1, st);
+      permute_rows<T, double>(o, N, Yo + (size_t)c0 * Nr, Nr, d_perm_plain, N, qq, 1, st);
     }
     if (tc_status_take(st)) throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
   }
   void probe(int level, int ncols, double* out) override {
     if (level < 1 || level > tau || ncols > c) throw Error(HODLR_EINVAL, "level / ncols");
-    probe_panel<T>(N, ncols, level, 0, seed, d_mask[level], R, N, st);
-    convert<T, double>(R, out, (long long)N * ncols, st);
+    probe_panel<T>(N, ncols, level, 0, seed, d_mask[level], d_rowid, R, N, st);
+    permute_rows<T, double>(R, N, out, Nr, d_real2pad, Nr, ncols, 0, st);   // real tree rows
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
   void densify(int which, double* out) override {
     if (!built) throw Error(HODLR_EINVAL, "no build");
     if ((long long)N * N > (1LL << 28)) throw Error(HODLR_EINVAL, "densify is for small N only");
-    // columns of the identity through the HODLR product
+    // columns of the identity (at the real rows) through the HODLR product, rows compacted to
+    // the real tree order
     int j = which == 0 || which == 1 || which == 4 ? -1 : which - 2;
     const int qd = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)wide * sizeof(T) / sizeof(double)));
-    for (int c0 = 0; c0 < N; c0 += qd) {
-      int qq = std::min(qd, N - c0);
-      double* col = out + (size_t)c0 * N;
-      fill<double>(col, 0.0, (long long)N * qq, st);
-      set_unit(col, c0, qq);
-      HODLR_CUDA(cudaMemcpyAsync(WZ, col, sizeof(double) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
-      matvec<double>(j, (const double*)WZ, N, col, N, qq, 0);
-      if (which == 1) axpby<double>(N, qq, -theta_built[3] / theta_built[0], (const double*)WZ, N,
-                                    1.0 / theta_built[0], col, N, st);
-      if (which == 4) HODLR_CUDA(cudaMemcpyAsync(col, WZ, sizeof(double) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
+    double* X = (double*)WZ;
+    double* Yp = (double*)WP;
+    for (int c0 = 0; c0 < Nr; c0 += qd) {
+      int qq = std::min(qd, Nr - c0);
+      fill<double>(X, 0.0, (long long)N * qq, st);
+      set_unit(X, c0, qq);
+      matvec<double>(j, (const double*)X, N, Yp, N, qq, 0);
+      if (which == 1) axpby<double>(N, qq, -theta_built[3] / theta_built[0], (const double*)X, N,
+                                    1.0 / theta_built[0], Yp, N, st);
+      if (which == 4) HODLR_CUDA(cudaMemcpyAsync(Yp, X, sizeof(double) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
+      permute_rows<double, double>(Yp, N, out + (size_t)c0 * Nr, Nr, d_real2pad, Nr, qq, 0, st);
     }
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
@@ -1321,14 +1352,14 @@ struct Engine : Base {
     if (!built || level < 1 || level > tau) throw Error(HODLR_EINVAL, "level");
     int wl = w[level];
     *w_out = wl;
-    size_t n = (what <= 1) ? (size_t)N * wl : (size_t)npairs(level) * wl * wl;
+    size_t n = (what <= 1) ? (size_t)Nr * wl : (size_t)npairs(level) * wl * wl;
     if ((int64_t)n > count) throw Error(HODLR_EINVAL, "count");
     double* tmp = vec_d2;
-    if (what == 0) {
-      convert<T, double>(F[level], (double*)WZ, (long long)n, st);
+    if (what <= 1) {
+      // panels in the real tree order (padding rows dropped)
+      if (what == 0) permute_rows<T, double>(F[level], N, (double*)WZ, Nr, d_real2pad, Nr, wl, 0, st);
+      else permute_rows<double, double>(U[level], N, (double*)WZ, Nr, d_real2pad, Nr, wl, 0, st);
       HODLR_CUDA(cudaMemcpyAsync(out, WZ, n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    } else if (what == 1) {
-      HODLR_CUDA(cudaMemcpyAsync(out, U[level], n * sizeof(double), cudaMemcpyDeviceToHost, st));
     } else {
       // recompute the child Grams of this level from F and U (as factor() does)
       GemmArgs g;
@@ -1354,9 +1385,9 @@ struct Engine : Base {
   }
   void solve_nat(const double* b, double* x) override {
     if (!built) throw Error(HODLR_EINVAL, "no build");
-    permute_rows<double, double>(b, N, vec_d, N, d_perm_plain, N, 1, 0, st);
+    permute_rows<double, double>(b, Nr, vec_d, N, d_perm_plain, N, 1, 0, st);
     solve_tree(vec_d, vec_d + N);
-    permute_rows<double, double>(vec_d + N, N, x, N, d_perm_plain, N, 1, 1, st);
+    permute_rows<double, double>(vec_d + N, N, x, Nr, d_perm_plain, N, 1, 1, st);
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
   void set_pivots(const int32_t* piv) override {
@@ -1382,9 +1413,9 @@ struct Engine : Base {
 // small kernels local to the engine
 namespace {
 template <class T>
-__global__ void identity_blocks_kernel(const int* bounds, int nl, T* S, long long ld) {
+__global__ void identity_blocks_kernel(const int* counts, int nl, T* S, long long ld) {
   int b = blockIdx.x;
-  int lo = bounds[b], n = bounds[b + 1] - lo;
+  int lo = b * nl, n = counts[b];   // leaf slot b: its real rows first, then padding rows
   for (int i = threadIdx.x; i < n; i += blockDim.x) S[lo + i + (size_t)i * ld] = T(1);
 }
 // rows [p*stride, p*stride + m) of pair p: columns j >= rank[p] set to zero
@@ -1396,17 +1427,17 @@ __global__ void zero_pad_cols_kernel(int m, long long stride, int wl, const int*
   int i = (int)(e % m), j = (int)(e / m);
   if (j >= rank[p]) rows[p * stride + i + (size_t)j * ld] = T(0);
 }
-__global__ void identity_cols_kernel(const int* bounds, double* S, long long ld, int j0, int qq) {
+__global__ void identity_cols_kernel(const int* counts, int nl, double* S, long long ld, int j0, int qq) {
   int b = blockIdx.x;
-  int lo = bounds[b], n = bounds[b + 1] - lo;
+  int lo = b * nl, n = counts[b];
   for (int jj = threadIdx.x; jj < qq; jj += blockDim.x)
     if (j0 + jj < n) S[lo + j0 + jj + (size_t)jj * ld] = 1.0;
 }
 template <class TS, class TD>
-__global__ void scatter_leaf_cols_kernel(const int* bounds, int nl, const TS* E, long long lde, int j0, int qq,
+__global__ void scatter_leaf_cols_kernel(const int* counts, int nl, const TS* E, long long lde, int j0, int qq,
                                          TD* Ablk) {
   int b = blockIdx.y;
-  int lo = bounds[b], n = bounds[b + 1] - lo;
+  int lo = b * nl, n = counts[b];
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)nl * qq) return;
   int i = (int)(e % nl), jj = (int)(e / nl);
@@ -1429,9 +1460,10 @@ __global__ void symmetrize_blocks_kernel(int nl, V* Ablk) {
   Ab[i + (size_t)j * nl] = v;
   Ab[j + (size_t)i * nl] = v;
 }
-__global__ void unit_cols_kernel(double* col, long long N, int c0, int qq) {
+// column j of X (ld N) = the unit vector of real tree position c0 + j
+__global__ void unit_cols_kernel(double* col, long long N, const int* real2pad, int c0, int qq) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < qq) col[c0 + j + (size_t)j * N] = 1.0;
+  if (j < qq) col[real2pad[c0 + j] + (size_t)j * N] = 1.0;
 }
 __global__ void scale_sum_kernel(const double* x, int n, double* out, double scale) {
   __shared__ double red[32];
@@ -1450,7 +1482,7 @@ __global__ void scale_sum_kernel(const double* x, int n, double* out, double sca
 }  // namespace
 
 template <class T> void Engine<T>::identity_blocks(T* Sl) {
-  identity_blocks_kernel<T><<<nleaves, 256, 0, st>>>(d_leafb, leaf, Sl, N);
+  identity_blocks_kernel<T><<<nleaves, 256, 0, st>>>(d_leafreal, leaf, Sl, N);
   check_launch("identity_blocks");
 }
 template <class T> void Engine<T>::zero_pad_cols(int l, int wl, T* rows) {
@@ -1460,12 +1492,12 @@ template <class T> void Engine<T>::zero_pad_cols(int l, int wl, T* rows) {
   check_launch("zero_pad_cols");
 }
 template <class T> void Engine<T>::identity_cols(double* Sx, int j0, int qq) {
-  identity_cols_kernel<<<nleaves, 64, 0, st>>>(d_leafb, Sx, N, j0, qq);
+  identity_cols_kernel<<<nleaves, 64, 0, st>>>(d_leafreal, leaf, Sx, N, j0, qq);
   check_launch("identity_cols");
 }
 template <class T> template <class TS, class TD> void Engine<T>::scatter_leaf_cols(const TS* E, int j0, int qq, TD* Ablk) {
   dim3 g(cdiv((long long)leaf * qq, 256), nleaves);
-  scatter_leaf_cols_kernel<TS, TD><<<g, 256, 0, st>>>(d_leafb, leaf, E, N, j0, qq, Ablk);
+  scatter_leaf_cols_kernel<TS, TD><<<g, 256, 0, st>>>(d_leafreal, leaf, E, N, j0, qq, Ablk);
   check_launch("scatter_leaf_cols");
 }
 template <class T> template <class V> void Engine<T>::symmetrize_blocks(V* Ablk) {
@@ -1474,7 +1506,7 @@ template <class T> template <class V> void Engine<T>::symmetrize_blocks(V* Ablk)
   check_launch("symmetrize_blocks");
 }
 template <class T> void Engine<T>::set_unit(double* col, int c0, int qq) {
-  unit_cols_kernel<<<cdiv(qq, 64), 64, 0, st>>>(col, N, c0, qq);
+  unit_cols_kernel<<<cdiv(qq, 64), 64, 0, st>>>(col, N, d_real2pad, c0, qq);
   check_launch("unit_cols");
 }
 template <class T> void Engine<T>::sum_doubles_scaled(double* x, int n, double* out, double scale) {
@@ -1548,9 +1580,9 @@ int hodlr_plan(const hodlr_model* m, const hodlr_opts* o, int64_t* dims_out, int
   try {
     // the engine's constructor builds the tree on the host and touches no device
     std::unique_ptr<Base> b(make_engine(m, o, nullptr));
-    dims_out[0] = b->N; dims_out[1] = b->tau; dims_out[2] = b->leaf; dims_out[3] = b->c; dims_out[4] = b->cap;
+    dims_out[0] = b->Nr; dims_out[1] = b->tau; dims_out[2] = b->leaf; dims_out[3] = b->c; dims_out[4] = b->cap;
     dims_out[5] = b->nleaves;
-    if (perm_out) std::memcpy(perm_out, b->perm64.data(), sizeof(int64_t) * b->N);
+    if (perm_out) std::memcpy(perm_out, b->perm64.data(), sizeof(int64_t) * b->Nr);
   } catch (const Error& x) {
     return x.code;
   } catch (const std::bad_alloc&) {
@@ -1633,12 +1665,12 @@ int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, con
 }
 int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out) {
   if (!h || !h->e || !perm_out) return HODLR_EINVAL;
-  std::memcpy(perm_out, h->e->perm64.data(), sizeof(int64_t) * h->e->N);
+  std::memcpy(perm_out, h->e->perm64.data(), sizeof(int64_t) * h->e->Nr);
   return HODLR_OK;
 }
 int hodlr_dims(const hodlr_ctx* h, int64_t* out) {
   if (!h || !h->e || !out) return HODLR_EINVAL;
-  out[0] = h->e->N; out[1] = h->e->tau; out[2] = h->e->leaf; out[3] = h->e->c; out[4] = h->e->cap;
+  out[0] = h->e->Nr; out[1] = h->e->tau; out[2] = h->e->leaf; out[3] = h->e->c; out[4] = h->e->cap;
   out[5] = h->e->nleaves;
   return HODLR_OK;
 }

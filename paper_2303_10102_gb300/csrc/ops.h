@@ -116,9 +116,10 @@ template <class T> void alg2_core(int nb, int w, const T* Yp, T* M2, cudaStream_
 template <class TI, class TO>
 void leaf_trsm(int nleaves, int nl, const double* L, const TI* in, long long ldi, TO* out, long long ldo, int q,
                cudaStream_t st);
-// symmetrise and gather leaf blocks: A_b = (E_b + E_b^T)/2, E_b = E[rows of leaf b, 0:n_b]
+// symmetrise and gather leaf blocks: A_b = (E_b + E_b^T)/2, E_b = E[b nl + (0:n_b), 0:n_b] with
+// n_b = counts[b] real rows in leaf slot b; the padding part of the nl x nl block is the identity
 template <class TS, class TD>
-void extract_leaves(int nleaves, int nl, const int* bounds, const TS* E, long long lde, TD* A,
+void extract_leaves(int nleaves, int nl, const int* counts, const TS* E, long long lde, TD* A,
                     cudaStream_t st);
 
 // ------------------------------------------------------------------------------ reductions
@@ -145,10 +146,11 @@ struct PhysicsDesc {
   int L1, L2;     // four-step split of a 1-D embedding longer than 4096 (L = L1*L2)
 };
 // Philox probe panel R^(level): N x ncols in tree order; row i non-zero iff it lies in the
-// right child of its level pair (right_child[i] = level mask bit).
+// right child of its level pair (right_child[i] = level mask bit).  The counter of row i is
+// rowid[i] (its position in the cluster tree without padding rows), or i when rowid is null.
 template <class T>
 void probe_panel(int N, int ncols, int level, int stream_id, uint64_t seed, const unsigned char* mask,
-                 T* out, long long ld, cudaStream_t st);
+                 const int* rowid, T* out, long long ld, cudaStream_t st);
 // Matern embedding spectra (real parts, in the FFT's internal order):
 //   lam[0] for K_u, lam[1] for dK_u/dell.  Computes kernel values, then forward FFT.
 template <class T>

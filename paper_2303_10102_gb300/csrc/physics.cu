@@ -47,13 +47,15 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 
 template <class T>
 __global__ void probe_kernel(int N, int level, int stream_id, uint32_t k0, uint32_t k1,
-                             const unsigned char* mask, T* out, long long ld) {
+                             const unsigned char* mask, const int* rowid, T* out, long long ld) {
   const int j = blockIdx.y;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   T z = T(0);
   if (mask[i]) {
-    uint32_t c[4] = {(uint32_t)i, (uint32_t)j, (uint32_t)level, (uint32_t)stream_id};
+    // the counter is the row's position in the cluster tree (without padding rows)
+    const uint32_t row = rowid ? (uint32_t)rowid[i] : (uint32_t)i;
+    uint32_t c[4] = {row, (uint32_t)j, (uint32_t)level, (uint32_t)stream_id};
     philox4x32_10(c, k0, k1);
     if constexpr (sizeof(T) == 8) {
       double u1 = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6) + 1.0) * 0x1p-53;
@@ -754,16 +756,18 @@ int ilog2(int n) {
 
 // ================================================================== launchers
 template <class T>
-void probe_panel(int N, int ncols, int level, int stream_id, uint64_t seed, const unsigned char* mask, T* out,
-                 long long ld, cudaStream_t st) {
+void probe_panel(int N, int ncols, int level, int stream_id, uint64_t seed, const unsigned char* mask,
+                 const int* rowid, T* out, long long ld, cudaStream_t st) {
   if (N <= 0 || ncols <= 0) return;
   dim3 g(cdiv(N, 256), ncols);
   probe_kernel<T><<<g, 256, 0, st>>>(N, level, stream_id, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32),
-                                     mask, out, ld);
+                                     mask, rowid, out, ld);
   check_launch("probe_panel");
 }
-template void probe_panel<double>(int, int, int, int, uint64_t, const unsigned char*, double*, long long, cudaStream_t);
-template void probe_panel<float>(int, int, int, int, uint64_t, const unsigned char*, float*, long long, cudaStream_t);
+template void probe_panel<double>(int, int, int, int, uint64_t, const unsigned char*, const int*, double*, long long,
+                                  cudaStream_t);
+template void probe_panel<float>(int, int, int, int, uint64_t, const unsigned char*, const int*, float*, long long,
+                                 cudaStream_t);
 
 template <class T> void twiddles(int L, T* tw, cudaStream_t st) {
   twiddle_kernel<T><<<cdiv(std::max(L / 2, 1), 256), 256, 0, st>>>(L, (typename CT<T>::C*)tw);

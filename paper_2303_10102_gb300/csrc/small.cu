@@ -383,9 +383,9 @@ __global__ void alg2_core_kernel(int w, const T* Ypall, T* M2all) {
 }
 
 template <class TS, class TD>
-__global__ void extract_leaves_kernel(int nl, const int* bounds, const TS* E, long long lde, TD* A) {
+__global__ void extract_leaves_kernel(int nl, const int* counts, const TS* E, long long lde, TD* A) {
   const int b = blockIdx.y;
-  const int lo = bounds[b], n = bounds[b + 1] - lo;
+  const int lo = b * nl, n = counts[b];   // leaf slot b: its real rows first, then padding rows
   TD* Ab = A + (size_t)b * nl * nl;
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)nl * nl) return;
@@ -470,8 +470,12 @@ __global__ void permute_rows_kernel(const TS* src, long long lds, TD* dst, long 
   const int j = blockIdx.y;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (scatter) dst[perm[i] + (size_t)j * ldd] = (TD)src[i + (size_t)j * lds];
-  else dst[i + (size_t)j * ldd] = (TD)src[perm[i] + (size_t)j * lds];
+  const int p = perm[i];   // -1: a padding row of the tree layout (no natural row)
+  if (scatter) {
+    if (p >= 0) dst[p + (size_t)j * ldd] = (TD)src[i + (size_t)j * lds];
+  } else {
+    dst[i + (size_t)j * ldd] = p >= 0 ? (TD)src[p + (size_t)j * lds] : TD(0);
+  }
 }
 
 template <class T>
@@ -583,9 +587,9 @@ template void alg2_core<double>(int, int, const double*, double*, cudaStream_t);
 template void alg2_core<float>(int, int, const float*, float*, cudaStream_t);
 
 template <class TS, class TD>
-void extract_leaves(int nleaves, int nl, const int* bounds, const TS* E, long long lde, TD* A, cudaStream_t st) {
+void extract_leaves(int nleaves, int nl, const int* counts, const TS* E, long long lde, TD* A, cudaStream_t st) {
   dim3 g(cdiv((long long)nl * nl, 256), nleaves);
-  extract_leaves_kernel<TS, TD><<<g, 256, 0, st>>>(nl, bounds, E, lde, A);
+  extract_leaves_kernel<TS, TD><<<g, 256, 0, st>>>(nl, counts, E, lde, A);
   check_launch("extract_leaves");
 }
 template void extract_leaves<double, double>(int, int, const int*, const double*, long long, double*, cudaStream_t);

@@ -57,6 +57,14 @@ SMALL = {
     # leaves of 128: the blocked leaf Cholesky and the two-level block inversion of the factors
     "1d-leaf128": synth.small_workload(dim=1, G=2048, nvar=1, nu=1.5, theta=(1.0, 0.1, 5.0, 1e-3), leaf=128,
                                        cap=10, c=12),
+    # uneven cluster trees (median splits of sizes that are not leaf x 2^tau): leaves of 62/63
+    # points, bivariate leaves of 31/32 points per variable, and a 23^2 grid (leaves of 33/34)
+    "1d-uneven": synth.small_workload(dim=1, G=1000, nvar=1, nu=1.5, theta=(1.0, 0.1, 5.0, 1e-3), leaf=64,
+                                      cap=12, c=16),
+    "1d-biv-uneven": synth.small_workload(dim=1, G=1001, nvar=2, nu=0.5, theta=(1.3, 0.07, 8.0, 2e-3), leaf=64,
+                                          cap=10, c=14),
+    "2d-uneven": synth.small_workload(dim=2, G=23, nvar=1, nu=0.5, theta=(1.0, 0.1, 8.0, 1e-3), leaf=64, cap=24,
+                                      c=32, tol=1e-6),
 }
 
 

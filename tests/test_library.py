@@ -93,15 +93,32 @@ def test_tree_order_bit_exact_at_full_size(so_path, name):
     assert np.array_equal(perm, np.asarray(t.perm, dtype=np.int64))
 
 
-def test_plan_rejects_uneven_trees_and_bad_models(so_path):
+@pytest.mark.parametrize("dim,G,nvar,leaf", [(1, 99, 1, 32), (1, 1000, 1, 64), (1, 40961, 1, 64),
+                                               (1, 4097, 2, 128), (2, 23, 1, 64), (2, 45, 2, 128)])
+def test_uneven_trees_match_the_oracle_bit_exactly(so_path, dim, G, nvar, leaf):
+    """Median splits of a size that is not leaf x 2^tau (Sec. 3.2.2 index sets) give leaves whose
+    sizes differ by one: the library's plan equals the oracle's tree order bit for bit."""
+    import numpy as np
+    from oracle.tree import Tree
+    lib = plib.load()
+    dims = np.zeros(6, dtype=np.int64)
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    m = plib.Model(dim, (ctypes.c_int * 2)(G, G if dim == 2 else 1), nvar, 1.5, 0)
+    o = plib.Opts(leaf, 8, 4, 0.0, 1, 0.0)
+    t = Tree(dim, G, nvar, leaf)
+    perm = np.zeros(t.N, dtype=np.int64)
+    assert lib.hodlr_plan(ctypes.byref(m), ctypes.byref(o), dims.ctypes.data_as(P64), perm.ctypes.data_as(P64)) == 0
+    sizes = [hi - lo for lo, hi in t.leaves()]
+    assert dims[0] == t.N and dims[1] == t.tau and dims[5] == 2 ** t.tau and dims[2] == max(sizes)
+    assert np.array_equal(perm, np.asarray(t.perm, dtype=np.int64))
+
+
+def test_plan_rejects_bad_models(so_path):
     import numpy as np
     lib = plib.load()
     dims = np.zeros(6, dtype=np.int64)
     P64 = ctypes.POINTER(ctypes.c_int64)
-    # 99 points with leaves of 32 rows: the first split gives nodes of 49 and 50 points (an uneven tree)
-    m = plib.Model(1, (ctypes.c_int * 2)(99, 1), 1, 1.5, 0)
     o = plib.Opts(32, 8, 4, 0.0, 1, 0.0)
-    assert lib.hodlr_plan(ctypes.byref(m), ctypes.byref(o), dims.ctypes.data_as(P64), None) == -6   # ENOTIMPL
     bad = plib.Model(3, (ctypes.c_int * 2)(16, 16), 1, 1.5, 0)
     assert lib.hodlr_plan(ctypes.byref(bad), ctypes.byref(o), dims.ctypes.data_as(P64), None) == -1   # EINVAL
 
