@@ -27,7 +27,9 @@
 #include <cstring>
 #include <type_traits>
 #include <string>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <new>
 #include <vector>
@@ -68,6 +70,14 @@ struct Base {
   virtual void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) = 0;
   virtual void get_pivots(int32_t* piv) const = 0;
   virtual cudaStream_t stream() const = 0;
+  // Capture-safe evaluation (NLL and gradient) for CUDA-graph batching: no host
+  // synchronisation, static level widths (the rank cap), statuses left on the device; the
+  // results land in out() = {nll, g[0..3], status} once the captured work has run.
+  virtual void set_stream(cudaStream_t s) = 0;
+  virtual void set_graph_mode(bool on) = 0;
+  virtual void eval_graph(const double* theta, const double* y) = 0;
+  virtual const double* graph_out() const = 0;
+  uint64_t serial = 0;                       // unique per context (graph cache keys)
   // N: rows of the (padded) tree layout; Nr: rows of K (natural order).  An uneven cluster
   // tree (median splits of a size that is not leaf x 2^tau) is laid out with every leaf in a
   // slot of the largest leaf's size: the real rows of a leaf come first in its slot, the rest
@@ -98,6 +108,9 @@ struct Engine : Base {
   PhysicsDesc ph;
   cudaStream_t st;
   cudaStream_t stream() const override { return st; }
+  void set_stream(cudaStream_t s) override { st = s; }
+  bool graph_mode = false;
+  void set_graph_mode(bool on) override { graph_mode = on; if (on) built = false; }
   // tree
   std::vector<std::vector<int>> bnd;     // per depth: node boundaries (2^d + 1)
   int* d_perm_plain = nullptr;           // tree-layout row -> natural index (-1 = padding)
@@ -403,6 +416,7 @@ struct Engine : Base {
   }
 
   void status_check(const char* what) {
+    if (graph_mode) return;   // left in d_status, read after the captured work has run
     int s = 0;
     HODLR_CUDA(cudaMemcpyAsync(&s, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     HODLR_CUDA(cudaStreamSynchronize(st));
@@ -606,11 +620,18 @@ struct Engine : Base {
       }
       pivoted_cholesky<T>(np, c, cap, cap, gram, thr, d_rank[l], d_piv[l], RinvJ, frozen ? 1 : 0, pwork, d_status, st);
       status_check("frozen pivots");
-      host_rank[l].resize(np);
-      HODLR_CUDA(cudaMemcpyAsync(host_rank[l].data(), d_rank[l], np * sizeof(int), cudaMemcpyDeviceToHost, st));
-      HODLR_CUDA(cudaStreamSynchronize(st));
       int wl = 0;
-      for (int r : host_rank[l]) wl = std::max(wl, r);
+      if (graph_mode) {
+        // static width: the rank cap (columns beyond a pair's own rank stay zero), so that the
+        // captured work does not depend on a value read back from the device
+        host_rank[l].assign(np, cap);
+        wl = cap;
+      } else {
+        host_rank[l].resize(np);
+        HODLR_CUDA(cudaMemcpyAsync(host_rank[l].data(), d_rank[l], np * sizeof(int), cudaMemcpyDeviceToHost, st));
+        HODLR_CUDA(cudaStreamSynchronize(st));
+        for (int r : host_rank[l]) wl = std::max(wl, r);
+      }
       w[l] = wl;
       fill<T>(F[l], T(0), (long long)N * cap, st);
       fill<T>(dF[0][l], T(0), (long long)N * cap, st);
@@ -685,7 +706,8 @@ struct Engine : Base {
     }
     build_leaves();
     factor();
-    if (tc_status_take(st)) throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
+    if (!graph_mode && tc_status_take(st))
+      throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
     for (int k = 0; k < 4; ++k) theta_built[k] = theta[k];
     built = true;
   }
@@ -733,9 +755,9 @@ struct Engine : Base {
       offdiag(1, tau, -1, Sl, N, nl, E[0], N);
       offdiag(1, tau, 0, Sl, N, nl, E[1], N);
       offdiag(1, tau, 1, Sl, N, nl, E[2], N);
-      extract_leaves<T, double>(nleaves, nl, d_leafreal, E[0], N, Afp, st);
-      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[1], N, dA[0], st);
-      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[2], N, dA[1], st);
+      extract_leaves<T, double>(nleaves, nl, d_leafreal, E[0], N, Afp, 1.0, st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[1], N, dA[0], 0.0, st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[2], N, dA[1], 0.0, st);
     }
     convert<double, T>(Afp, A, (long long)nleaves * nl * nl, st);
     // FP64 leaf Cholesky, log-det and inverse
@@ -806,8 +828,8 @@ struct Engine : Base {
       apply(Sl, N, nl, nullptr, E[1], E[2], N);
       offdiag(1, tau, 0, Sl, N, nl, E[1], N);
       offdiag(1, tau, 1, Sl, N, nl, E[2], N);
-      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[1], N, dA[0], st);
-      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[2], N, dA[1], st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[1], N, dA[0], 0.0, st);
+      extract_leaves<T, T>(nleaves, nl, d_leafreal, E[2], N, dA[1], 0.0, st);
     }
     // leaf blocks of K~ in FP64-class arithmetic, in column chunks
     const int qcl = std::max(1, std::min(64, wide / 4));
@@ -1007,6 +1029,7 @@ struct Engine : Base {
     // total log-det: leaves + nodes (Sylvester)
     sum_doubles(leaflog, nleaves, res + 0, 0, st);
     for (int l = 1; l <= tau; ++l) sum_doubles(d_nodelog[l], npairs(l), res + 0, 1, st);
+    if (graph_mode) return;   // res[0] is read on the device
     HODLR_CUDA(cudaMemcpyAsync(&logdet, res, sizeof(double), cudaMemcpyDeviceToHost, st));
     HODLR_CUDA(cudaStreamSynchronize(st));
     if (!std::isfinite(logdet)) throw Error(HODLR_ENUMERIC, "log-determinant is not finite");
@@ -1173,6 +1196,7 @@ struct Engine : Base {
           }
         }
     }
+    if (graph_mode) return;   // the accumulators are read on the device
     double h[12];
     HODLR_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
     HODLR_CUDA(cudaStreamSynchronize(st));
@@ -1296,6 +1320,29 @@ struct Engine : Base {
     if (fisher) for (int j = 0; j < 16; ++j) fin = fin && std::isfinite(fisher[j]);
     if (!fin) throw Error(HODLR_ENUMERIC, "non-finite result");
   }
+
+  // NLL and gradient without host synchronisation (for capture into a CUDA graph); the same
+  // arithmetic as eval(), with the scalar assembly done by finalize_nll_grad on the device.
+  void eval_graph(const double* theta, const double* y) override {
+    if (!graph_mode) throw Error(HODLR_EINVAL, "eval_graph outside graph mode");
+    derivatives_supported();
+    build(theta);
+    HODLR_CUDA(cudaMemsetAsync(d_status + 1, 0, sizeof(int), st));
+    check_finite<double>(y, Nr, d_status + 1, st);
+    permute_rows<double, double>(y, Nr, vec_d, N, d_perm_plain, N, 1, 0, st);
+    solve_tree(vec_d, vec_d + N);
+    double* alpha = vec_d + N;
+    dot_columns<double, double>(N, 1, vec_d, N, alpha, N, res + 40, st);
+    dot_columns<double, double>(N, 1, alpha, N, alpha, N, res + 41, st);
+    for (int j = 0; j < 2; ++j) {
+      matvec<double>(j, alpha, N, vec_d2, N, 1, 0);
+      dot_columns<double, double>(N, 1, alpha, N, vec_d2, N, res + 42 + j, st);
+    }
+    traces_impl(false, nullptr, nullptr);
+    finalize_nll_grad(theta);
+  }
+  const double* graph_out() const override { return res + 200; }
+  void finalize_nll_grad(const double* theta);
 
   // ---------------------------------------------------------------- test entry points
   void apply_nat(const double* theta, int which, const double* X, double* Yo, int ncols) override {
@@ -1481,6 +1528,34 @@ __global__ void scale_sum_kernel(const double* x, int n, double* out, double sca
 }
 }  // namespace
 
+// {nll, g_sigma2, g_ell, g_kappa, g_tau2, status} from the device accumulators of one evaluation
+// (the formulas of eval(): log-det res[0], y^T a res[40], a^T a res[41], a^T K~_j a res[42..43],
+// tr(K~^{-1} M) res[16..18] for M = (I, K~_ell, K~_kappa)).
+__global__ void finalize_nll_grad_kernel(const double* res, const int* status, double nr, double npad, double s2,
+                                         double t2, double* out) {
+  if (threadIdx.x != 0) return;
+  const double ldet = res[0], a_y = res[40], a_a = res[41];
+  const double t0 = res[16] - npad;
+  const double trj[4] = {(nr - t2 * t0) / s2, res[17], res[18], t0};
+  const double quad[4] = {(a_y - t2 * a_a) / s2, res[42], res[43], a_a};
+  const double nll = 0.5 * nr * log(2.0 * M_PI) + 0.5 * ldet + 0.5 * a_y;
+  out[0] = nll;
+  bool fin = isfinite(nll);
+  for (int j = 0; j < 4; ++j) {
+    out[1 + j] = 0.5 * trj[j] - 0.5 * quad[j];
+    fin = fin && isfinite(out[1 + j]);
+  }
+  double st = 0.0;
+  if (status[0] != 0) st = (double)status[0];
+  else if (status[1] != 0 || !fin) st = (double)HODLR_ENUMERIC;
+  out[5] = st;
+}
+template <class T> void Engine<T>::finalize_nll_grad(const double* theta) {
+  finalize_nll_grad_kernel<<<1, 32, 0, st>>>(res, d_status, (double)Nr, (double)npad, theta[0], theta[3],
+                                              res + 200);
+  check_launch("finalize_nll_grad");
+}
+
 template <class T> void Engine<T>::identity_blocks(T* Sl) {
   identity_blocks_kernel<T><<<nleaves, 256, 0, st>>>(d_leafreal, leaf, Sl, N);
   check_launch("identity_blocks");
@@ -1601,6 +1676,8 @@ int hodlr_create(hodlr_ctx** out, const hodlr_model* m, const hodlr_opts* o, voi
   if (!h) return HODLR_ENOMEM;
   try {
     h->e = make_engine(m, o, (cudaStream_t)cuda_stream);
+    static std::atomic<uint64_t> next_serial{1};
+    h->e->serial = next_serial++;
     Arena ar;
     ar.plan = false;
     ar.base = (char*)workspace;
@@ -1650,17 +1727,151 @@ int hodlr_eval(hodlr_ctx* h, const double* theta, const double* y, double* nll_o
     if (fisher_out) std::memcpy(fisher_out, f, sizeof(f));
   });
 }
+}  // extern "C"
+
+namespace {
+// One CUDA graph holding the NLL and gradient evaluations of a list of contexts: every
+// context's evaluation is captured on a branch stream of its own (forked from and joined to the
+// first context's stream), so that the evaluations of small datasets run side by side, and the
+// whole list replays as one graph launch.  Cached for the last (contexts, theta, y) list.
+struct BatchGraph {
+  std::vector<uint64_t> serial;
+  std::vector<double> theta;
+  std::vector<const double*> y;
+  cudaStream_t root = nullptr;              // the library's own stream: graphs are captured and
+                                             // launched there, ordered after / before the contexts'
+  cudaGraphExec_t exec = nullptr;
+  long long nkernels = 0;
+  std::vector<cudaStream_t> br;
+  std::vector<cudaEvent_t> ev;   // ev[0] fork, ev[1 + i] join of branch i
+  ~BatchGraph() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    serial.clear();
+  }
+  void ensure_resources(int nb) {
+    if (!root) HODLR_CUDA(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+    while ((int)br.size() < nb) {
+      cudaStream_t s;
+      HODLR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      br.push_back(s);
+    }
+    while ((int)ev.size() < nb + 2) {
+      cudaEvent_t e;
+      HODLR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ev.push_back(e);
+    }
+  }
+};
+BatchGraph g_batch;
+std::mutex g_batch_mu;
+
+void batch_capture(hodlr_ctx* const* hs, int nb, const double* thetas, const double* const* ys) {
+  BatchGraph& B = g_batch;
+  B.reset();
+  std::vector<cudaStream_t> saved(nb);
+  for (int i = 0; i < nb; ++i) {
+    saved[i] = hs[i]->e->stream();
+    hs[i]->e->set_graph_mode(true);
+  }
+  auto restore = [&] {
+    for (int i = 0; i < nb; ++i) {
+      hs[i]->e->set_stream(saved[i]);
+      hs[i]->e->set_graph_mode(false);   // the next single call rebuilds in the ordinary mode
+    }
+  };
+  const long long k0 = g_kernel_launches;
+  cudaGraph_t graph = nullptr;
+  HODLR_CUDA(cudaStreamBeginCapture(B.root, cudaStreamCaptureModeRelaxed));
+  try {
+    HODLR_CUDA(cudaEventRecord(B.ev[0], B.root));
+    for (int i = 0; i < nb; ++i) {
+      HODLR_CUDA(cudaStreamWaitEvent(B.br[i], B.ev[0], 0));
+      hs[i]->e->set_stream(B.br[i]);
+      hs[i]->e->eval_graph(thetas + 4 * (size_t)i, ys[i]);
+      HODLR_CUDA(cudaEventRecord(B.ev[1 + i], B.br[i]));
+      HODLR_CUDA(cudaStreamWaitEvent(B.root, B.ev[1 + i], 0));
+    }
+  } catch (...) {
+    cudaStreamEndCapture(B.root, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    restore();
+    throw;
+  }
+  cudaError_t e = cudaStreamEndCapture(B.root, &graph);
+  restore();
+  if (e != cudaSuccess) throw Error(HODLR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&B.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    B.exec = nullptr;
+    throw Error(HODLR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  B.nkernels = g_kernel_launches - k0;
+  g_kernel_launches = k0;
+  for (int i = 0; i < nb; ++i) B.serial.push_back(hs[i]->e->serial);
+  B.theta.assign(thetas, thetas + 4 * (size_t)nb);
+  B.y.assign(ys, ys + nb);
+}
+}  // namespace
+
+extern "C" {
+
 int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, const double* const* ys, double* nll_out,
                          double* grad_out) {
   if (!hs || nb <= 0 || !thetas || !ys || !nll_out || !grad_out) return HODLR_EINVAL;
-  // results are collected first, so that a failed call leaves the outputs untouched
-  std::vector<double> v(nb), g(4 * (size_t)nb);
   for (int i = 0; i < nb; ++i) {
-    int rc = guarded(hs[i], [&] { hs[i]->e->eval(thetas + 4 * i, ys[i], &v[i], &g[4 * (size_t)i], nullptr); });
-    if (rc) return rc;
+    if (!hs[i] || !hs[i]->e || !ys[i]) return HODLR_EINVAL;
+    for (int k = 0; k < 4; ++k)
+      if (!(thetas[4 * i + k] > 0.0) || !std::isfinite(thetas[4 * i + k])) return HODLR_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return HODLR_EINVAL;   // one branch per context
   }
-  std::memcpy(nll_out, v.data(), sizeof(double) * nb);
-  std::memcpy(grad_out, g.data(), sizeof(double) * 4 * (size_t)nb);
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchGraph& B = g_batch;
+  std::vector<double> out(6 * (size_t)nb);
+  int rc = HODLR_OK;
+  try {
+    B.ensure_resources(nb);
+    bool same = B.exec && (int)B.serial.size() == nb;
+    for (int i = 0; same && i < nb; ++i) same = B.serial[i] == hs[i]->e->serial && B.y[i] == ys[i];
+    for (int k = 0; same && k < 4 * nb; ++k) same = B.theta[k] == thetas[k];
+    if (!same) batch_capture(hs, nb, thetas, ys);
+    // the graph runs after the work already queued on the contexts' streams (y, for instance) ...
+    cudaEvent_t order = B.ev[nb + 1];
+    for (int i = 0; i < nb; ++i) {
+      HODLR_CUDA(cudaEventRecord(order, hs[i]->e->stream()));
+      HODLR_CUDA(cudaStreamWaitEvent(B.root, order, 0));
+    }
+    HODLR_CUDA(cudaGraphLaunch(B.exec, B.root));
+    // ... and before the work queued on them later
+    HODLR_CUDA(cudaEventRecord(order, B.root));
+    for (int i = 0; i < nb; ++i) HODLR_CUDA(cudaStreamWaitEvent(hs[i]->e->stream(), order, 0));
+    g_kernel_launches += B.nkernels;
+    for (int i = 0; i < nb; ++i)
+      HODLR_CUDA(cudaMemcpyAsync(out.data() + 6 * (size_t)i, hs[i]->e->graph_out(), 6 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, B.root));
+    HODLR_CUDA(cudaStreamSynchronize(B.root));
+    if (tc_status_take(B.root)) throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
+    for (int i = 0; i < nb && rc == HODLR_OK; ++i)
+      if (out[6 * (size_t)i + 5] != 0.0) {
+        rc = (int)out[6 * (size_t)i + 5];
+        hs[i]->err = "batched evaluation: a Cholesky factorization failed or a result is not finite";
+      }
+  } catch (const Error& x) {
+    hs[0]->err = x.what();
+    B.reset();
+    return x.code;
+  } catch (const std::bad_alloc&) {
+    B.reset();
+    return HODLR_ENOMEM;
+  }
+  if (rc != HODLR_OK) return rc;
+  for (int i = 0; i < nb; ++i) {
+    nll_out[i] = out[6 * (size_t)i];
+    for (int j = 0; j < 4; ++j) grad_out[4 * (size_t)i + j] = out[6 * (size_t)i + 1 + j];
+  }
   return HODLR_OK;
 }
 int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out) {

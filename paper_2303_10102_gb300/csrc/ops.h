@@ -117,9 +117,10 @@ template <class TI, class TO>
 void leaf_trsm(int nleaves, int nl, const double* L, const TI* in, long long ldi, TO* out, long long ldo, int q,
                cudaStream_t st);
 // symmetrise and gather leaf blocks: A_b = (E_b + E_b^T)/2, E_b = E[b nl + (0:n_b), 0:n_b] with
-// n_b = counts[b] real rows in leaf slot b; the padding part of the nl x nl block is the identity
+// n_b = counts[b] real rows in leaf slot b; the padding part of the nl x nl block is pad * I
+// (1 for leaves of K~, 0 for leaves of a derivative matrix)
 template <class TS, class TD>
-void extract_leaves(int nleaves, int nl, const int* counts, const TS* E, long long lde, TD* A,
+void extract_leaves(int nleaves, int nl, const int* counts, const TS* E, long long lde, TD* A, double pad,
                     cudaStream_t st);
 
 // ------------------------------------------------------------------------------ reductions

@@ -383,7 +383,7 @@ __global__ void alg2_core_kernel(int w, const T* Ypall, T* M2all) {
 }
 
 template <class TS, class TD>
-__global__ void extract_leaves_kernel(int nl, const int* counts, const TS* E, long long lde, TD* A) {
+__global__ void extract_leaves_kernel(int nl, const int* counts, const TS* E, long long lde, TD* A, double pad) {
   const int b = blockIdx.y;
   const int lo = b * nl, n = counts[b];   // leaf slot b: its real rows first, then padding rows
   TD* Ab = A + (size_t)b * nl * nl;
@@ -392,7 +392,7 @@ __global__ void extract_leaves_kernel(int nl, const int* counts, const TS* E, lo
   int i = (int)(e % nl), j = (int)(e / nl);
   double v = 0.0;
   if (i < n && j < n) v = 0.5 * ((double)E[lo + i + (size_t)j * lde] + (double)E[lo + j + (size_t)i * lde]);
-  else if (i == j) v = 1.0;   // pad ragged leaves with the identity (decoupled)
+  else if (i == j) v = pad;   // padding rows: unit diagonal in K~ (decoupled), zero in dK~
   Ab[i + (size_t)j * nl] = (TD)v;
 }
 
@@ -587,14 +587,18 @@ template void alg2_core<double>(int, int, const double*, double*, cudaStream_t);
 template void alg2_core<float>(int, int, const float*, float*, cudaStream_t);
 
 template <class TS, class TD>
-void extract_leaves(int nleaves, int nl, const int* counts, const TS* E, long long lde, TD* A, cudaStream_t st) {
+void extract_leaves(int nleaves, int nl, const int* counts, const TS* E, long long lde, TD* A, double pad,
+                    cudaStream_t st) {
   dim3 g(cdiv((long long)nl * nl, 256), nleaves);
-  extract_leaves_kernel<TS, TD><<<g, 256, 0, st>>>(nl, counts, E, lde, A);
+  extract_leaves_kernel<TS, TD><<<g, 256, 0, st>>>(nl, counts, E, lde, A, pad);
   check_launch("extract_leaves");
 }
-template void extract_leaves<double, double>(int, int, const int*, const double*, long long, double*, cudaStream_t);
-template void extract_leaves<float, double>(int, int, const int*, const float*, long long, double*, cudaStream_t);
-template void extract_leaves<float, float>(int, int, const int*, const float*, long long, float*, cudaStream_t);
+template void extract_leaves<double, double>(int, int, const int*, const double*, long long, double*, double,
+                                             cudaStream_t);
+template void extract_leaves<float, double>(int, int, const int*, const float*, long long, double*, double,
+                                            cudaStream_t);
+template void extract_leaves<float, float>(int, int, const int*, const float*, long long, float*, double,
+                                           cudaStream_t);
 
 template <class T>
 void trace_products(int nb, int n, const int* sizes, const T* X, long long ldx, long long sX, const T* Y,
