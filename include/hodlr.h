@@ -52,6 +52,13 @@ extern "C" {
                                 otherwise); FP64-class leaf sketch of K~, leaf
                                 Cholesky, SMW cores, factorization sweeps and
                                 log-det (FP64 or double-float accumulation)      */
+#define HODLR_MIXED_BF16 2   /* FP64 storage and FP64 physics recurrences, with the
+                                dense products (DST of the operator solve, peeling,
+                                projection, leaf, factorization and trace products)
+                                carried out on the BF16 tcgen05 tensor cores as
+                                exact products of 7-bit digit slices with FP32
+                                accumulation (error ~2^-41 of the row/column-scaled
+                                bound, FP64-class); small products stay FP64      */
 
 typedef struct hodlr_ctx hodlr_ctx;
 
@@ -61,7 +68,7 @@ typedef struct hodlr_ctx hodlr_ctx;
  *   nvar     1: y = A^{-1} u   (K = A^{-1} K_u A^{-1} + tau2 I)
  *            2: y = (u, A^{-1} u)  (K = L K_u L^T + tau2 I, L = [I; A^{-1}])
  *   nu       Matern smoothness 0.5 or 1.5 (eq. whittle covariance, no sqrt(2 nu))
- *   precision HODLR_FP64 or HODLR_MIXED_FP32                                      */
+ *   precision HODLR_FP64, HODLR_MIXED_FP32 or HODLR_MIXED_BF16                    */
 typedef struct {
   int dim;
   int grid[2];
@@ -229,6 +236,25 @@ int hodlr_reset_kernel_count(hodlr_ctx* h);
  * counts 2).  Runs on the legacy default stream and synchronises it; allocates nothing.
  * HODLR_ETIMEOUT if an MMA completion wait gave up.  */
 int hodlr_peak(int which, double* tflops_out);
+
+/* FP64-class batched product on the BF16 tensor cores (the building block of HODLR_MIXED_BF16;
+ * a dense contraction in the paper's HODLR arithmetic, Table "HODLR operations", Sec. 3.1):
+ *   C_b = alpha op(A_b) op(B_map(b)) + beta C_b,  b = 0 .. batch-1,
+ * column-major FP64 device matrices: op(A_b) is M x K (A_b = A + b sA, ld lda, transposed when
+ * tA), op(B) is K x N (B_i = B + i sB, ld ldb, transposed when tB), map(b) = b, b^1, b>>1 for
+ * bmap = 0, 1, 2, C_b = C + b sC (ld ldc); sA = 0 (sB = 0) shares one A (B) among the batch.
+ * Each operand row (A) or column (B) is scaled by a power of two and cut into six balanced 7-bit
+ * digits held exactly in BF16; the 21 digit products with p + q <= 5 run on tcgen05 with FP32
+ * accumulation in tensor memory, exact for the three leading digit groups over 512-long chunks
+ * of K; the result is assembled in 64-bit integers and rounded once.  Error below ~2^-40 of
+ * sum_k max_k'|A_ik'| max_k'|B_k'j| (finite inputs).
+ * work: caller-owned device scratch of work_bytes >= 64 MiB, 256-byte aligned (slice planes and
+ * split-K partials; larger problems are processed in batch and column chunks).  cuda_stream may
+ * be NULL.  Allocates nothing.  HODLR_ENOMEM if even one product does not fit work_bytes;
+ * HODLR_ETIMEOUT if a bounded wait gave up.  Synchronises the stream.  */
+int hodlr_dgemm_slices(int M, int N, int K, int batch, const double* A, long long lda, long long sA, int tA,
+                       const double* B, long long ldb, long long sB, int tB, int bmap, double alpha, double beta,
+                       double* C, long long ldc, long long sC, void* work, size_t work_bytes, void* cuda_stream);
 
 /* Failure-detection hook (the paper has no counterpart; for tests of the bounded waits).
  * Sets, on the current device, how many times each tensor-core CTA polls its FIRST operand

@@ -373,6 +373,11 @@ template <class TA, class TB, class TC, class Acc>
 void gemm(const GemmArgs& g, Scratch s, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   if (g.K > 0 && gemv_narrow<TA, TB, TC, Acc>(g, st)) return;
+  if constexpr (std::is_same<TA, double>::value && std::is_same<TB, double>::value &&
+                std::is_same<TC, double>::value && std::is_same<Acc, double>::value) {
+    // FP64-class products on the BF16 tensor cores (digit slices) when the context asks for them
+    if (g_oz_cfg.on && oz_gemm(g, g_oz_cfg.split.bytes > s.bytes ? g_oz_cfg.split : s, st)) return;
+  }
   if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
                 std::is_same<Acc, float>::value) {
     if (tf32x3_gemm_tn(g, s, st)) return;      // tensor cores, TMA-staged panels with K contiguous

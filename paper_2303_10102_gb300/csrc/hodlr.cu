@@ -74,10 +74,14 @@ struct Base {
   // synchronisation, static level widths (the rank cap), statuses left on the device; the
   // results land in out() = {nll, g[0..3], status} once the captured work has run.
   virtual void set_stream(cudaStream_t s) = 0;
+  // digit-slice tensor-core products for this context's FP64 GEMMs (HODLR_MIXED_BF16): set on
+  // entry to every call on the calling thread, cleared on exit
+  virtual void oz_enter(bool on) = 0;
   virtual void set_graph_mode(bool on) = 0;
   virtual void eval_graph(const double* theta, const double* y) = 0;
   virtual const double* graph_out() const = 0;
   uint64_t serial = 0;                       // unique per context (graph cache keys)
+  bool uses_slices = false;                  // HODLR_MIXED_BF16 context
   // N: rows of the (padded) tree layout; Nr: rows of K (natural order).  An uneven cluster
   // tree (median splits of a size that is not leaf x 2^tau) is laid out with every leaf in a
   // slot of the largest leaf's size: the real rows of a leaf come first in its slot, the rest
@@ -109,6 +113,13 @@ struct Engine : Base {
   cudaStream_t st;
   cudaStream_t stream() const override { return st; }
   void set_stream(cudaStream_t s) override { st = s; }
+  bool oz = false;                       // HODLR_MIXED_BF16
+  Scratch ozwork, ozsplit;
+  void oz_enter(bool on) override {
+    g_oz_cfg.on = on && oz;
+    g_oz_cfg.work = on && oz ? ozwork : Scratch{};
+    g_oz_cfg.split = on && oz ? ozsplit : Scratch{};
+  }
   bool graph_mode = false;
   void set_graph_mode(bool on) override { graph_mode = on; if (on) built = false; }
   // tree
@@ -175,6 +186,8 @@ struct Engine : Base {
 
   Engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t s_) {
     dim = m->dim; G = m->grid[0]; nvar = m->nvar; nu = m->nu; prec = m->precision;
+    oz = prec == HODLR_MIXED_BF16 && sizeof(T) == 8;
+    uses_slices = oz;
     leaf = o->leaf; cap = o->rank_or_cap; c = o->rank_or_cap + o->oversample; tol = o->tol; seed = o->seed;
     guard = o->guard > 0.0 ? o->guard : 1e-5;
     st = s_;
@@ -375,6 +388,16 @@ struct Engine : Base {
     Ucat = ar.take<double>(NN * (size_t)std::max(tau, 1) * cap);
     for (int l = 1; l <= tau; ++l) U[l] = Ucat + NN * (size_t)cap * (l - 1);
     d_status = ar.take<int>(8);
+    if (oz) {
+      // slice planes for one wide panel (six BF16 digits per FP64 value), at least 256 MB and
+      // at most 2 GiB; split-K partials of the long-K products
+      size_t ob = (size_t)14 * NN * std::max(wide, c) + ((size_t)1 << 26);
+      ob = std::min<size_t>(std::max<size_t>(ob, (size_t)1 << 28), (size_t)1 << 31);
+      ozwork.ptr = ar.take<char>(ob);
+      ozwork.bytes = ob;
+      ozsplit.bytes = (size_t)1 << 28;
+      ozsplit.ptr = ar.take<char>(ozsplit.bytes);
+    }
     size_t sbytes = std::max<size_t>(64u << 20, (size_t)4 * c * c * 8 * 640);
     scratch.ptr = ar.take<char>(sbytes);
     scratch.bytes = sbytes;
@@ -1604,8 +1627,15 @@ struct hodlr_ctx {
 
 template <class F> static int guarded(hodlr_ctx* h, F f) {
   if (!h || !h->e) return HODLR_EINVAL;
+  struct OzScope {   // the context's product path for this call, on this thread
+    Base* e;
+    explicit OzScope(Base* b) : e(b) { e->oz_enter(true); }
+    ~OzScope() { e->oz_enter(false); }
+  } scope(h->e);
   try {
     f();
+    if (h->e->uses_slices)
+      if (int t = oz_status_take(h->e->stream())) throw Error(t, "a tensor-core product gave up waiting for its operands");
     h->err.clear();
     return HODLR_OK;
   } catch (const Error& x) {
@@ -1622,7 +1652,7 @@ template <class F> static int guarded(hodlr_ctx* h, F f) {
 }
 
 static Base* make_engine(const hodlr_model* m, const hodlr_opts* o, cudaStream_t st) {
-  if (m->precision == HODLR_FP64) return new Engine<double>(m, o, st);
+  if (m->precision == HODLR_FP64 || m->precision == HODLR_MIXED_BF16) return new Engine<double>(m, o, st);
   if (m->precision == HODLR_MIXED_FP32) return new Engine<float>(m, o, st);
   throw Error(HODLR_EINVAL, "precision");
 }
@@ -1789,7 +1819,9 @@ void batch_capture(hodlr_ctx* const* hs, int nb, const double* thetas, const dou
     for (int i = 0; i < nb; ++i) {
       HODLR_CUDA(cudaStreamWaitEvent(B.br[i], B.ev[0], 0));
       hs[i]->e->set_stream(B.br[i]);
+      hs[i]->e->oz_enter(true);
       hs[i]->e->eval_graph(thetas + 4 * (size_t)i, ys[i]);
+      hs[i]->e->oz_enter(false);
       HODLR_CUDA(cudaEventRecord(B.ev[1 + i], B.br[i]));
       HODLR_CUDA(cudaStreamWaitEvent(B.root, B.ev[1 + i], 0));
     }
@@ -1853,7 +1885,8 @@ int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, con
       HODLR_CUDA(cudaMemcpyAsync(out.data() + 6 * (size_t)i, hs[i]->e->graph_out(), 6 * sizeof(double),
                                  cudaMemcpyDeviceToHost, B.root));
     HODLR_CUDA(cudaStreamSynchronize(B.root));
-    if (tc_status_take(B.root)) throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
+    if (tc_status_take(B.root) || oz_status_take(B.root))
+      throw Error(HODLR_ETIMEOUT, "a tensor-core product gave up waiting for its operands");
     for (int i = 0; i < nb && rc == HODLR_OK; ++i)
       if (out[6 * (size_t)i + 5] != 0.0) {
         rc = (int)out[6 * (size_t)i + 5];

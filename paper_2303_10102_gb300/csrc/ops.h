@@ -56,6 +56,21 @@ bool tf32x3_gemm_tn(const GemmArgs& g, Scratch s, cudaStream_t st);
 // matrices, B_b likewise (a stacked or single B when K is not a multiple of 32).  M >= 128,
 // leading dimensions multiples of 4.  Returns false (nothing launched) when not supported.
 bool tf32x3_gemm_nn(const GemmArgs& g, cudaStream_t st);
+// FP64-class product C_b = alpha op(A_b) op(B_map(b)) + beta C_b of FP64 operands on the BF16
+// tensor cores by exact digit slices (six 7-bit digits per operand; error about 2^-41 of
+// sum_k max|A_i.| max|B_.j|).  Used in place of the FP64 FMA product while g_oz_cfg.on is set
+// (this thread); its slicing planes live in g_oz_cfg.work, split-K partials in `split`.
+// Returns false (nothing launched) for shapes it does not take.
+struct OzConfig {
+  bool on = false;
+  Scratch work;    // slice planes and exponents
+  Scratch split;   // split-K partials (used when larger than the caller's scratch)
+};
+extern thread_local OzConfig g_oz_cfg;
+bool oz_eligible(const GemmArgs& g);
+bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st);
+bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st);   // without the size thresholds
+int oz_status_take(cudaStream_t st);   // HODLR_ETIMEOUT recorded by a product (and cleared), or 0
 // Ordered reduction of FP32 split-K partials into C (alpha, beta, offsets as in g).
 void splitk_reduce_f32(const GemmArgs& g, int nsplit, const float* part, cudaStream_t st);
 // hi = x with the low 13 mantissa bits cleared, lo = x - hi (exact); hi may alias x.

@@ -1,0 +1,636 @@
+// FP64-class products on the BF16 tensor cores (tcgen05 kind::f16) by exact digit slices.
+//
+// GB300 executes FP64 fused multiply-adds at about 1 TFLOP/s but BF16 tensor-core products at
+// about 2.4 PFLOP/s.  A product C = A B of FP64 matrices is carried out as follows (a slicing
+// scheme in the manner of Ozaki, Ogita, Oishi and Rump, with integer digit extraction):
+//   * every row i of A gets an exponent ea_i with max_k |A_ik| < 2^ea_i, every column j of B an
+//     exponent eb_j likewise;
+//   * the scaled row A_ik 2^(6 - ea_i), a number in (-64, 64), is rounded to a fixed-point
+//     integer with 35 fractional bits and cut into S = 6 balanced base-2^7 digits a_p in
+//     [-64, 64]:  A_ik ~ 2^(ea_i - 6) sum_p a_p 2^(-7p); B likewise (digits b_q);
+//   * plane p of A stores a_p 2^(-7p) as BF16 (exact: a digit has at most 7 significant bits),
+//     so that the tensor-core product of planes p and q is sum_k a_p b_q 2^(-7(p+q)), and all
+//     products of one "group" t = p + q are integer multiples of 2^(-7t);
+//   * the products with p + q <= S - 1 are accumulated in FP32 in tensor memory: groups t = 0,
+//     1, 2 in accumulators of their own, whose sums over a 512-long chunk of K stay below 2^23
+//     units and are therefore exact; groups t = 3, 4, 5 share one accumulator (their FP32
+//     rounding is below 2^-45 of the leading group);
+//   * after every chunk the exact group sums are converted to one 64-bit integer per element
+//     (units 2^-14), summed over the chunks exactly, and at the end combined with the tail
+//     group and the scales into the FP64 result (integer arithmetic, one rounding).
+// The dropped groups t >= 6 and the fixed-point rounding bound the error by about 2^-41 of
+// sum_k max_k'|A_ik'| max_k'|B_k'j| -- the accuracy class of double-float arithmetic -- at a
+// cost of 21 BF16 products.
+//
+// One CTA (8 warps) computes a 128 x 128 tile of C over a range of K (split across CTAs when the
+// tiles are few): TMA (cp.async.bulk.tensor, 64-byte swizzle) stages 32-wide K slices of all six
+// planes of A and B (96 KB per stage, two stages) behind mbarrier transaction counts; one thread
+// issues the 42 tcgen05.mma (M = 128, N = 128, K = 16) of a slice; the four accumulators fill
+// the 512 TMEM columns; every wait is bounded (a wait that gives up records HODLR_ETIMEOUT,
+// drains what was issued and frees the TMEM).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "../../include/hodlr.h"
+#include "common.cuh"
+#include "ops.h"
+
+namespace hodlr {
+namespace {
+
+constexpr int OZ_S = 6;                      // digit planes per operand
+constexpr int OZ_NPAIR = OZ_S * (OZ_S + 1) / 2;
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32;
+constexpr int OZ_KC = 512;                   // exactness chunk of K
+constexpr int OZ_THREADS = 256;
+constexpr int OZ_PLANE_A = OZ_BM * OZ_BK * 2;            // 8 KB per plane and slice
+constexpr int OZ_PLANE_B = OZ_BN * OZ_BK * 2;            // 8 KB
+constexpr int OZ_STAGE = OZ_S * (OZ_PLANE_A + OZ_PLANE_B);   // 96 KB
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
+constexpr int OZ_WAIT_LIMIT = 1 << 22;
+
+__device__ int g_oz_status;
+
+__device__ __forceinline__ uint32_t oz_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void oz_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_smem(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void oz_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(oz_smem(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, uint32_t ph) {
+  const uint32_t addr = oz_smem(bar);
+  for (int it = 0; it < OZ_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(ph)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void oz_tma3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(oz_smem(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(oz_smem(bar))
+      : "memory");
+}
+// K-major operand in shared memory with the 64-byte swizzle: rows of 64 bytes (32 BF16 values),
+// 8-row groups 512 bytes apart (tcgen05 shared-memory descriptor, version 1, swizzle mode 4).
+__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+__device__ __forceinline__ void oz_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void oz_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(oz_smem(bar))
+               : "memory");
+}
+__device__ __forceinline__ void oz_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void oz_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void oz_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- slicing
+// Operand view: element (b, r, k) at base[b * sb + r * sr + k * sk] (doubles).  The slice planes
+// are laid out [p][b][r][Kp] (BF16, K contiguous, Kp a multiple of 32, zero past K) and the
+// exponents [b][r].
+struct OzView {
+  const double* base;
+  long long sb, sr, sk;
+  int nb, R, K;
+};
+
+__device__ __forceinline__ int oz_biased_exp(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// exponent of every row: e = (largest biased exponent of the row) - 1023 + 1, so that all
+// |x| < 2^e; rows of zeros (or subnormals only) get the sentinel -2000
+__global__ void oz_rowexp_kernel(OzView v, int* ex) {
+  const int b = blockIdx.y;
+  const double* base = v.base + (size_t)b * v.sb;
+  if (v.sk == 1) {
+    // one warp per row, reading along k
+    const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * warps + wid;
+    if (r >= v.R) return;
+    int m = 0;
+    for (int k = lane; k < v.K; k += 32) m = max(m, oz_biased_exp(base[(size_t)r * v.sr + k]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) ex[(size_t)b * v.R + r] = m == 0 ? -2000 : m - 1023 + 1;
+  } else {
+    // one thread per row, threads of a warp on consecutive rows
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= v.R) return;
+    int m = 0;
+    for (int k = 0; k < v.K; ++k) m = max(m, oz_biased_exp(base[(size_t)r * v.sr + (size_t)k * v.sk]));
+    ex[(size_t)b * v.R + r] = m == 0 ? -2000 : m - 1023 + 1;
+  }
+}
+
+// fixed-point value F = round(x 2^(41 - e)) of |x| < 2^e (|F| <= 2^41), by integer operations
+__device__ __forceinline__ long long oz_fixed(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int be = (int)((bits >> 52) & 0x7ff);
+  if (be == 0 || e <= -1000) return 0;                       // zero or subnormal
+  const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);   // x = mant 2^(be - 1075)
+  // F = mant 2^(be - 1075 + 41 - e); the shift is right by sh = e + 1034 - be >= 12
+  const int sh = e + 1034 - be;
+  long long f = sh >= 63 ? 0 : ((mant + (1LL << (sh - 1))) >> sh);
+  return bits < 0 ? -f : f;
+}
+
+// digits of F: d_0 = round(F 2^-35), then the remainder in base 2^7, balanced (|d| <= 64)
+__device__ __forceinline__ void oz_digits(long long F, int (&d)[OZ_S]) {
+#pragma unroll
+  for (int p = 0; p < OZ_S - 1; ++p) {
+    const int sh = 7 * (OZ_S - 1 - p);
+    const long long q = (F + (1LL << (sh - 1))) >> sh;
+    d[p] = (int)q;
+    F -= q << sh;
+  }
+  d[OZ_S - 1] = (int)F;
+}
+
+// 32 (r) x 32 (k) tiles through shared memory: loads are coalesced along the operand's
+// contiguous direction, plane stores along k
+__global__ void oz_slice_kernel(OzView v, const int* ex, __nv_bfloat16* planes, int Kp) {
+  __shared__ double tile[32][33];
+  const int b = blockIdx.z;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  const double* base = v.base + (size_t)b * v.sb;
+  for (int j = ty; j < 32; j += 8) {
+    if (v.sk == 1) {   // k contiguous: threads along k
+      const int r = r0 + j, k = k0 + tx;
+      tile[j][tx] = (r < v.R && k < v.K) ? base[(size_t)r * v.sr + k] : 0.0;
+    } else {           // threads along r
+      const int r = r0 + tx, k = k0 + j;
+      tile[tx][j] = (r < v.R && k < v.K) ? base[(size_t)r * v.sr + (size_t)k * v.sk] : 0.0;
+    }
+  }
+  __syncthreads();
+  const size_t plane = (size_t)v.nb * v.R * Kp;
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + j, k = k0 + tx;
+    if (r >= v.R || k >= Kp) continue;
+    const int e = ex[(size_t)b * v.R + r];
+    int d[OZ_S];
+    oz_digits(oz_fixed(tile[j][tx], e), d);
+    const size_t o = ((size_t)b * v.R + r) * Kp + k;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) planes[p * plane + o] = __float2bfloat16_rn(ldexpf((float)d[p], -7 * p));
+  }
+}
+
+// ---------------------------------------------------------------- the product kernel
+struct OzParams {
+  int M, N, K, Kp;          // per product; Kp: padded K of the planes (multiple of 32)
+  int nbA, nbB;             // distinct A / B operands (planes per operand: OZ_S)
+  int bmap;                 // B operand of product b: b, b^1, b>>1 (or 0 when nbB == 1)
+  int nsplit;               // split of K across CTAs: one OZ_KC chunk each
+  const int *exA, *exB;     // exponents [nbA][M], [nbB][N]
+  double alpha, beta;
+  double* C;                // nsplit == 1: C_b = C + b*sC, leading dimension ldc
+  long long ldc, sC;
+  double* part;             // nsplit > 1: partials ((b*nsplit + s) * M * N) + i + j*M
+};
+
+// x 2^e2 for an integer x, rounded to nearest (even) into a double, by integer operations (the
+// FP64 pipes of this GPU are slow); results below the normal range flush to zero
+__device__ __forceinline__ double oz_i64_to_f64(long long x, int e2) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = x < 0 ? 0x8000000000000000ULL : 0ULL;
+  unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int msb = 63 - __clzll((long long)a);
+  int ex = msb + e2;
+  unsigned long long m;
+  if (msb > 52) {
+    const int sh = msb - 52;
+    unsigned long long q = a >> sh, rem = a & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ULL))) {
+      ++q;
+      if (q >> 53) { q >>= 1; ++ex; }
+    }
+    m = q;
+  } else {
+    m = a << (52 - msb);
+  }
+  if (ex + 1023 <= 0) return 0.0;
+  if (ex + 1023 >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ULL));
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const OzParams p) {
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(sm + OZ_STAGES * OZ_STAGE);
+  uint64_t* done = full + OZ_STAGES;
+  uint32_t* tslot = (uint32_t*)(done + OZ_STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  const int b = blockIdx.z / p.nsplit, sp = blockIdx.z % p.nsplit;
+  const int bA = p.nbA == 1 ? 0 : b;
+  const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
+  // one exactness chunk of K per CTA (longer K is split across CTAs)
+  const int kbeg = sp * OZ_KC, kend = min(p.Kp, kbeg + OZ_KC);
+  const int nk = (kend - kbeg) / OZ_BK;           // slices (kbeg, kend multiples of 32)
+
+  if (tid == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      oz_mbar_init(&full[s], 1);
+      oz_mbar_init(&done[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(oz_smem(tslot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  oz_fence_before();
+  __syncthreads();
+  oz_fence_after();
+  const uint32_t tmem = *tslot;
+  // D FP32; A, B BF16, K-major; N = 128; M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                         ((uint32_t)(OZ_BM >> 4) << 24);
+  auto planeA = [&](int s, int q) { return sm + s * OZ_STAGE + q * OZ_PLANE_A; };
+  auto planeB = [&](int s, int q) { return sm + s * OZ_STAGE + OZ_S * OZ_PLANE_A + q * OZ_PLANE_B; };
+  auto issue_loads = [&](int kt) {
+    const int s = kt & 1;
+    oz_expect_tx(&full[s], OZ_STAGE);
+    const int kx = kbeg + kt * OZ_BK;
+#pragma unroll
+    for (int q = 0; q < OZ_S; ++q) {
+      oz_tma3(planeA(s, q), &mapA, kx, m0, q * p.nbA + bA, &full[s]);
+      oz_tma3(planeB(s, q), &mapB, kx, n0, q * p.nbB + bB, &full[s]);
+    }
+  };
+
+  const int wq = warp & 3, wh = warp >> 2;   // TMEM lane quarter and column half of this warp
+  bool ok = true;
+  int issued = 0, committed = 0;
+  if (tid == 0 && nk > 0) {
+    issue_loads(0);
+    issued = 1;
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    const int s = kt & 1;
+    if (tid == 0 && kt + 1 < nk) {
+      // the other stage was last read by the products of slice kt - 1
+      if (kt >= 1 && !oz_wait(&done[s ^ 1], ((kt - 1) >> 1) & 1)) ok = false;
+      if (ok) {
+        issue_loads(kt + 1);
+        issued = kt + 2;
+      }
+    }
+    if (tid == 0 && ok) {
+      if (!oz_wait(&full[s], (kt >> 1) & 1)) ok = false;
+      if (ok) {
+        oz_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {   // two K = 16 steps per 32-wide slice: 32 bytes apart
+#pragma unroll
+          for (int pa = 0; pa < OZ_S; ++pa) {
+#pragma unroll
+            for (int pb = 0; pb < OZ_S - pa; ++pb) {
+              const int t = pa + pb, g = t < 3 ? t : 3;
+              // the first product into each accumulator overwrites it
+              const bool first = kt == 0 && kk == 0 && pa == 0 && (g < 3 || t == 3);
+              oz_mma(tmem + (uint32_t)(g * OZ_BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
+                     oz_desc(oz_smem(planeB(s, pb)) + 32 * kk), idesc, first ? 0u : 1u);
+            }
+          }
+        }
+        oz_commit(&done[s]);
+        committed = kt + 1;
+      }
+    }
+  }
+  if (nk > 0 && ok && tid == 0) ok = oz_wait(&done[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+  ok = __syncthreads_and(ok) != 0;
+  if (ok) {
+    oz_fence_after();
+    const int row = m0 + 32 * wq + lane;
+    const int ea = row < p.M ? p.exA[(size_t)bA * p.M + row] : 0;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t col0 = (uint32_t)(64 * wh + 32 * h);
+      const uint32_t lanes = (uint32_t)(32 * wq) << 16;
+      uint32_t r0[32], r1[32];
+      long long V[32];
+      if (nk > 0) {
+        // groups 0..2 hold exact multiples of 2^(-7g) below 2^(23 - 7g): times 2^14 integers
+        oz_ld32(tmem + lanes + col0, r0);
+        oz_ld32(tmem + lanes + (uint32_t)OZ_BN + col0, r1);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          V[j] = (long long)(__uint_as_float(r0[j]) * 16384.0f) + (long long)(__uint_as_float(r1[j]) * 16384.0f);
+        oz_ld32(tmem + lanes + (uint32_t)(2 * OZ_BN) + col0, r0);
+        oz_ld32(tmem + lanes + (uint32_t)(3 * OZ_BN) + col0, r1);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) V[j] += (long long)(__uint_as_float(r0[j]) * 16384.0f);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) { V[j] = 0; r1[j] = 0u; }
+      }
+      if (row >= p.M) continue;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + (int)col0 + j;
+        if (col < p.N) {
+          // value = 2^(ea + eb - 12) (V 2^-14 + tail): V (exact, units 2^-14) and the tail group
+          // (FP32, below 2^-21 of the leading groups' scale) join in one 64-bit integer whose
+          // unit 2^-(14 + sh) is as fine as the larger of the two allows
+          const int eb = p.exB[(size_t)bB * p.N + col];
+          const float tl = __uint_as_float(r1[j]);
+          const long long Vj = V[j];
+          const unsigned long long av = Vj < 0 ? (unsigned long long)(-Vj) : (unsigned long long)Vj;
+          int bl = av ? 64 - __clzll((long long)av) : 0;
+          if (tl != 0.0f) bl = max(bl, ilogbf(tl) + 15);
+          const int sh = min(60, 61 - bl);
+          const long long W = (long long)(av << sh) * (Vj < 0 ? -1 : 1) + __float2ll_rn(ldexpf(tl, 14 + sh));
+          const double v = (ea < -1000 || eb < -1000) ? 0.0 : oz_i64_to_f64(W, ea + eb - 12 - 14 - sh);
+          if (p.nsplit == 1) {
+            double* c = p.C + (size_t)b * p.sC + (size_t)col * p.ldc + row;
+            double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
+            if (p.beta != 0.0) out = p.beta == 1.0 ? *c + out : fma(p.beta, *c, out);
+            *c = out;
+          } else {
+            p.part[((size_t)b * p.nsplit + sp) * ((size_t)p.M * p.N) + (size_t)col * p.M + row] = v;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(&g_oz_status, HODLR_ETIMEOUT);
+    for (int kt = committed - 1; kt >= 0 && kt >= committed - 2; --kt) oz_wait(&done[kt & 1], (kt >> 1) & 1);
+    for (int kt = issued - 1; kt >= committed && kt >= 0; --kt) oz_wait(&full[kt & 1], (kt >> 1) & 1);
+  }
+  oz_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    oz_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ordered reduction of the split-K partials (FP64), then alpha / beta
+__global__ void oz_reduce_kernel(int M, int N, int nsplit, const double* part, double alpha, double beta, double* C,
+                                 long long ldc, long long sC) {
+  const int b = blockIdx.y;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)M * N) return;
+  const int i = (int)(e % M), j = (int)(e / M);
+  const double* pp = part + (size_t)b * nsplit * ((size_t)M * N) + e;
+  double v = 0.0;
+  for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * M * N];
+  double* c = C + (size_t)b * sC + (size_t)j * ldc + i;
+  double out = alpha * v;
+  if (beta != 0.0) out = fma(beta, *c, out);
+  *c = out;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn oz_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &r) == cudaSuccess &&
+        r == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)q;
+  });
+  return fn;
+}
+// planes [S * nb][R][Kp] BF16: a 3-D map with boxes of 32 (K) x rows x 1, 64-byte swizzle; rows
+// beyond R read as zeros
+bool oz_map(CUtensorMap* m, const __nv_bfloat16* planes, int Kp, int R, int nplanes, int box_rows) {
+  EncodeTiledFn fn = oz_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)nplanes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * (cuuint64_t)R};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)planes, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void oz_slice(const OzView& v, int Kp, int* ex, __nv_bfloat16* planes, cudaStream_t st) {
+  if (v.sk == 1) {
+    dim3 g(cdiv(v.R, 8), v.nb);
+    oz_rowexp_kernel<<<g, 256, 0, st>>>(v, ex);
+  } else {
+    dim3 g(cdiv(v.R, 128), v.nb);
+    oz_rowexp_kernel<<<g, 128, 0, st>>>(v, ex);
+  }
+  check_launch("oz_rowexp");
+  dim3 g(Kp / 32, cdiv(v.R, 32), v.nb);
+  oz_slice_kernel<<<g, dim3(32, 8), 0, st>>>(v, ex, planes, Kp);
+  check_launch("oz_slice");
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host entry points
+thread_local OzConfig g_oz_cfg;
+
+bool oz_eligible(const GemmArgs& g) {
+  if (!g_oz_cfg.on || !g_oz_cfg.work.ptr) return false;
+  if (g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
+  if (g.batch > 65535) return false;
+  // products this small are cheaper on the FP64 pipes than the slicing passes
+  const double mnk = (double)g.M * g.N * g.K * g.batch;
+  return g.M >= 32 && g.N >= 32 && g.K >= 32 && mnk >= (double)(1 << 22);
+}
+
+// bytes of slicing workspace for a batch of nb products (A and B planes, exponents)
+static size_t oz_bytes(int nbA, int M, int nbB, int N, int Kp) {
+  return align256((size_t)OZ_S * nbA * M * Kp * 2) + align256((size_t)OZ_S * nbB * N * Kp * 2) +
+         align256((size_t)nbA * M * 4) + align256((size_t)nbB * N * 4);
+}
+
+bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st) {
+  if (!oz_eligible(g)) return false;
+  return oz_gemm_any(g, split, st);
+}
+
+bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
+  if (!g_oz_cfg.work.ptr || g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
+  const Scratch w = g_oz_cfg.work;
+  const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  const size_t nsp = (size_t)cdiv(Kp, OZ_KC);   // one 512-long chunk of K per CTA
+  const bool sharedA = g.sA == 0, sharedB = g.sB == 0;
+  const bool paired = g.bmap != BMAP_ID && !sharedB;
+  auto nbB_of = [&](int nb) { return sharedB ? 1 : (g.bmap == BMAP_SHR1 ? (nb + 1) / 2 : nb); };
+  auto need = [&](int nb, int nc) {   // workspace and partials of a (batch chunk, column chunk)
+    const size_t planes = oz_bytes(sharedA ? 1 : nb, g.M, nbB_of(nb), nc, Kp);
+    const size_t part = nsp > 1 ? (size_t)nb * g.M * nc * nsp * sizeof(double) : 0;
+    return planes <= w.bytes && part <= split.bytes;
+  };
+  // batch chunk (even when products are paired), then column chunk (multiple of the tile)
+  int bchunk = g.batch;
+  while (bchunk > (paired ? 2 : 1) && !need(bchunk, g.N)) {
+    bchunk = (bchunk + 1) / 2;
+    if (paired) bchunk += bchunk & 1;
+  }
+  int nchunk = g.N;
+  while (nchunk > OZ_BN && !need(bchunk, nchunk)) nchunk = ((nchunk / 2 + OZ_BN - 1) / OZ_BN) * OZ_BN;
+  if (!need(bchunk, nchunk)) return false;
+  HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  for (int b0 = 0; b0 < g.batch; b0 += bchunk) {
+    const int nb = std::min(bchunk, g.batch - b0);
+    const int nbA = sharedA ? 1 : nb, nbB = nbB_of(nb);
+    char* base = (char*)w.ptr;
+    __nv_bfloat16* pA = (__nv_bfloat16*)base;
+    base += align256((size_t)OZ_S * nbA * g.M * Kp * 2);
+    int* eA = (int*)base;
+    base += align256((size_t)nbA * g.M * 4);
+    __nv_bfloat16* pB = (__nv_bfloat16*)base;
+    base += align256((size_t)OZ_S * nbB * nchunk * Kp * 2);
+    int* eB = (int*)base;
+    // A: rows i of op(A), along k
+    OzView va;
+    va.base = (const double*)g.A + (size_t)b0 * g.sA;
+    va.sb = g.sA; va.nb = nbA; va.R = g.M; va.K = g.K;
+    if (g.tA) { va.sr = g.lda; va.sk = 1; } else { va.sr = 1; va.sk = g.lda; }
+    oz_slice(va, Kp, eA, pA, st);
+    CUtensorMap ma;
+    if (!oz_map(&ma, pA, Kp, g.M, OZ_S * nbA, OZ_BM)) throw Error(HODLR_ECUDA, "oz_gemm: tensor map");
+    const int bB0 = sharedB ? 0 : (g.bmap == BMAP_SHR1 ? b0 / 2 : b0);
+    for (int j0 = 0; j0 < g.N; j0 += nchunk) {
+      const int nc = std::min(nchunk, g.N - j0);
+      // B: rows j of op(B)^T (columns j0 .. j0 + nc of op(B)), along k
+      OzView vb;
+      const long long coff = g.tB ? (long long)j0 : (long long)j0 * g.ldb;
+      vb.base = (const double*)g.B + (size_t)bB0 * g.sB + coff;
+      vb.sb = g.sB; vb.nb = nbB; vb.R = nc; vb.K = g.K;
+      if (g.tB) { vb.sr = 1; vb.sk = g.ldb; } else { vb.sr = g.ldb; vb.sk = 1; }
+      oz_slice(vb, Kp, eB, pB, st);
+      CUtensorMap mb;
+      if (!oz_map(&mb, pB, Kp, nc, OZ_S * nbB, OZ_BN)) throw Error(HODLR_ECUDA, "oz_gemm: tensor map");
+      const int nsplit = (int)nsp;
+      OzParams p{};
+      p.M = g.M; p.N = nc; p.K = g.K; p.Kp = Kp; p.nbA = nbA; p.nbB = nbB;
+      p.bmap = sharedB ? BMAP_ID : g.bmap; p.nsplit = nsplit;
+      p.exA = eA; p.exB = eB; p.alpha = g.alpha; p.beta = g.beta;
+      p.C = (double*)g.C + (size_t)b0 * g.sC + (size_t)j0 * g.ldc; p.ldc = g.ldc; p.sC = g.sC;
+      p.part = (double*)split.ptr;
+      if ((long long)nb * nsplit > 65535) throw Error(HODLR_EINVAL, "oz_gemm: batch too large");
+      dim3 grid(cdiv(g.M, OZ_BM), cdiv(nc, OZ_BN), nb * nsplit);
+      const bool prof = g_prof.on && g_prof.n < g_prof.cap;
+      if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+      oz_mma_kernel<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, p);
+      check_launch("oz_mma_kernel");
+      if (prof) {
+        cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+        if (g_prof.shape) {
+          int* sh = g_prof.shape + 7 * g_prof.n;
+          sh[0] = g.M; sh[1] = nc; sh[2] = g.K; sh[3] = nb; sh[4] = g.tA; sh[5] = g.tB; sh[6] = 5;
+        }
+        ++g_prof.n;
+        g_prof.flops += 2.0 * (double)g.M * nc * g.K * nb;
+        g_prof.bytes += ((double)g.M * g.K + (double)g.K * nc + (double)g.M * nc * (g.beta != 0.0 ? 2 : 1)) * 8.0 * nb;
+      }
+      if (nsplit > 1) {
+        dim3 rg(cdiv((long long)g.M * nc, 256), nb);
+        oz_reduce_kernel<<<rg, 256, 0, st>>>(g.M, nc, nsplit, p.part, g.alpha, g.beta, p.C, g.ldc, g.sC);
+        check_launch("oz_reduce");
+      }
+    }
+  }
+  return true;
+}
+
+int oz_status_take(cudaStream_t st) {
+  int v = 0, zero = 0;
+  HODLR_CUDA(cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+  HODLR_CUDA(cudaStreamSynchronize(st));
+  if (v) HODLR_CUDA(cudaMemcpyToSymbolAsync(g_oz_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+  return v;
+}
+
+}  // namespace hodlr
+
+using namespace hodlr;
+
+extern "C" int hodlr_dgemm_slices(int M, int N, int K, int batch, const double* A, long long lda, long long sA,
+                                  int tA, const double* B, long long ldb, long long sB, int tB, int bmap,
+                                  double alpha, double beta, double* C, long long ldc, long long sC, void* work,
+                                  size_t work_bytes, void* cuda_stream) {
+  if (M < 0 || N < 0 || K < 0 || batch < 1 || !A || !B || !C || !work || bmap < 0 || bmap > 2) return HODLR_EINVAL;
+  if (((uintptr_t)work & 255) || work_bytes < (64u << 20)) return HODLR_EINVAL;
+  if (M == 0 || N == 0) return HODLR_OK;
+  try {
+    GemmArgs g;
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.lda = lda; g.sA = sA; g.tA = tA ? 1 : 0;
+    g.B = B; g.ldb = ldb; g.sB = sB; g.tB = tB ? 1 : 0; g.bmap = bmap;
+    g.C = C; g.ldc = ldc; g.sC = sC;
+    g.alpha = alpha; g.beta = beta; g.batch = batch;
+    // the first quarter of the workspace holds split-K partials, the rest the slice planes
+    Scratch split{work, work_bytes / 4};
+    OzConfig saved = g_oz_cfg;
+    g_oz_cfg.on = true;
+    g_oz_cfg.work = Scratch{(char*)work + work_bytes / 4, work_bytes - work_bytes / 4};
+    bool done = false;
+    try {
+      // any shape: the eligibility thresholds of the engine do not apply to this call
+      done = K > 0 ? oz_gemm_any(g, split, (cudaStream_t)cuda_stream) : false;
+    } catch (...) {
+      g_oz_cfg = saved;
+      throw;
+    }
+    g_oz_cfg = saved;
+    if (!done && K > 0) return HODLR_ENOMEM;
+    if (K == 0) {
+      // C = beta C through the plain kernel path
+      gemm<double, double, double, double>(g, split, (cudaStream_t)cuda_stream);
+    }
+    HODLR_CUDA(cudaGetLastError());
+    if (oz_status_take((cudaStream_t)cuda_stream)) return HODLR_ETIMEOUT;
+  } catch (const Error& x) {
+    return x.code;
+  }
+  return HODLR_OK;
+}

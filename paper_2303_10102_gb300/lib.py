@@ -16,7 +16,7 @@ from . import build as _build
 HODLR_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ENOTPD", -4: "ENUMERIC", -5: "ETIMEOUT", -6: "ENOTIMPL",
           -7: "ECUDA"}
-PRECISION = {"fp64": 0, "fp32": 1, "mixed": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 WHICH = {"K": 0, "sigma2": 1, "ell": 2, "kappa": 3, "tau2": 4}
 
 _LIB = None
@@ -70,6 +70,9 @@ SIGNATURES = {
     "hodlr_reset_kernel_count": (C.c_int, [_P]),
     "hodlr_debug_wait_limit": (C.c_int, [C.c_int]),
     "hodlr_peak": (C.c_int, [C.c_int, _D]),
+    "hodlr_dgemm_slices": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_longlong, C.c_longlong, C.c_int,
+                                     _P, C.c_longlong, C.c_longlong, C.c_int, C.c_int, C.c_double, C.c_double, _P,
+                                     C.c_longlong, C.c_longlong, _P, C.c_size_t, _P]),
     "hodlr_apply_static": (C.c_int, [C.c_int, C.c_double, _D, _P, _P, C.c_int, _P]),
     "hodlr_last_error": (C.c_char_p, [_P]),
     "hodlr_destroy": (None, [_P]),

@@ -1,4 +1,5 @@
-"""Parity of the mixed-precision path at the benched configuration's settings.
+"""Parity of the mixed-precision path (HODLR_MIXED_BF16: FP64-class products on the BF16 tensor
+cores) at the benched configuration's settings.
 
 Workload P2: C2's model and HODLR settings (2-D univariate, Matern nu = 1/2, kappa = 8, leaf 256,
 rank cap 128, c = 136 probe columns, tol = guard = 1e-6, FP32/TF32 bulk) on a 128^2 grid
@@ -77,7 +78,7 @@ def errors(f, g, F, d):
 def p2():
     from paper_2303_10102_gb300 import Hodlr
     w = synth.workload("P2")
-    h = Hodlr(w.dim, w.G, w.nvar, w.nu, "fp32", w.leaf, w.cap, w.c - w.cap, w.tol, w.seed_probe, device=DEV,
+    h = Hodlr(w.dim, w.G, w.nvar, w.nu, "bf16", w.leaf, w.cap, w.c - w.cap, w.tol, w.seed_probe, device=DEV,
               guard=w.guard)
     y = torch.as_tensor(synth.simulate_y(w), device=DEV)
     yield w, h, y

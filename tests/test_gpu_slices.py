@@ -1,0 +1,122 @@
+"""FP64-class products on the BF16 tensor cores (hodlr_dgemm_slices, the product of the
+HODLR_MIXED_BF16 path) against FP64 products of the same operands.
+
+  * exactness: integer operands whose products and sums are exact in FP64 give bit-exact results,
+    with K inside one 512-long chunk (exact FP32 accumulation of the digit groups in tensor
+    memory) and across chunks (split K, FP64 reduction of exact partials);
+  * accuracy: random operands with rows and columns scaled over six decades, every layout
+    (transposes, batches with strides, a shared A, paired B operands, alpha and beta), ragged
+    sizes; the error is checked against the slicing bound K 2^-38 max|A_i.| max|B_.j| and
+    normwise against 1e-12;
+  * zero rows and columns give exact zeros.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def slices(A, B, M, N, K, batch=1, lda=None, sA=None, tA=0, ldb=None, sB=None, tB=0, bmap=0, alpha=1.0, beta=0.0,
+           C=None, ldc=None, sC=None, work_mb=256):
+    from paper_2303_10102_gb300 import lib as plib
+    lib = plib.load()
+    work = torch.empty(work_mb << 20, dtype=torch.uint8, device=DEV)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.hodlr_dgemm_slices(M, N, K, batch, ctypes.c_void_p(A.data_ptr()), lda, sA, tA,
+                                ctypes.c_void_p(B.data_ptr()), ldb, sB, tB, bmap, alpha, beta,
+                                ctypes.c_void_p(C.data_ptr()), ldc, sC, ctypes.c_void_p(work.data_ptr()),
+                                work.numel(), st)
+    torch.cuda.synchronize()
+    return rc
+
+
+def colmajor(x):
+    """device buffer holding the column-major storage of a 2-D array"""
+    return torch.as_tensor(np.asfortranarray(x).ravel(order="F"), device=DEV)
+
+
+@pytest.mark.parametrize("K", [37, 512, 1000, 2048])
+def test_integer_operands_are_exact(K):
+    rng = np.random.default_rng(K)
+    M, N = 150, 130
+    A = rng.integers(-1000, 1001, size=(M, K)).astype(np.float64)
+    B = rng.integers(-1000, 1001, size=(K, N)).astype(np.float64)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    C = torch.zeros(M * N, dtype=torch.float64, device=DEV)
+    assert slices(colmajor(A), colmajor(B), M, N, K, 1, M, 0, 0, K, 0, 0, 0, 1.0, 0.0, C, M, 0) == 0
+    got = C.cpu().numpy().reshape(N, M).T
+    assert np.array_equal(got, ref)
+
+
+def _bound(A, B):
+    K = A.shape[1]
+    return K * 2.0 ** -38 * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :]
+
+
+def _scaled(rng, m, n):
+    return (rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-3, 3, size=(m, 1))
+            * 10.0 ** rng.uniform(-3, 3, size=(1, n)))
+
+
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_random_scaled_operands_all_layouts(tA, tB):
+    rng = np.random.default_rng(10 + 2 * tA + tB)
+    M, N, K = 200, 300, 777
+    A = _scaled(rng, M, K)
+    B = _scaled(rng, K, N)
+    C0 = rng.standard_normal((M, N))
+    Ast = colmajor(A.T if tA else A)
+    Bst = colmajor(B.T if tB else B)
+    C = colmajor(C0)
+    alpha, beta = -1.5, 0.5
+    rc = slices(Ast, Bst, M, N, K, 1, K if tA else M, 0, tA, N if tB else K, 0, tB, 0, alpha, beta, C, M, 0)
+    assert rc == 0
+    got = C.cpu().numpy().reshape(N, M).T
+    ref = alpha * (A @ B) + beta * C0
+    err = np.abs(got - ref)
+    assert np.all(err <= 1.5 * _bound(A, B) + 1e-15 * np.abs(ref)), err.max()
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_batched_strided_shared_and_paired_operands():
+    rng = np.random.default_rng(3)
+    M, N, K, nb = 130, 70, 600, 4
+    As = [_scaled(rng, M, K) for _ in range(nb)]
+    Bs = [_scaled(rng, K, N) for _ in range(nb)]
+    # products b use B_(b^1): stored as K x N blocks
+    A = torch.cat([colmajor(a) for a in As])
+    B = torch.cat([colmajor(b) for b in Bs])
+    C = torch.zeros(nb * M * N, dtype=torch.float64, device=DEV)
+    assert slices(A, B, M, N, K, nb, M, M * K, 0, K, K * N, 0, 1, 1.0, 0.0, C, M, M * N) == 0
+    got = C.cpu().numpy().reshape(nb, N, M).transpose(0, 2, 1)
+    for b in range(nb):
+        ref = As[b] @ Bs[b ^ 1]
+        assert np.all(np.abs(got[b] - ref) <= 1.5 * _bound(As[b], Bs[b ^ 1])), b
+    # one A shared by the batch (sA = 0), B_(b>>1)
+    C2 = torch.zeros(nb * M * N, dtype=torch.float64, device=DEV)
+    assert slices(A, B, M, N, K, nb, M, 0, 0, K, K * N, 0, 2, 1.0, 0.0, C2, M, M * N) == 0
+    got = C2.cpu().numpy().reshape(nb, N, M).transpose(0, 2, 1)
+    for b in range(nb):
+        ref = As[0] @ Bs[b >> 1]
+        assert np.all(np.abs(got[b] - ref) <= 1.5 * _bound(As[0], Bs[b >> 1])), b
+
+
+def test_zero_rows_columns_and_chunked_workspace():
+    rng = np.random.default_rng(4)
+    M, N, K = 257, 1000, 300
+    A = _scaled(rng, M, K)
+    B = _scaled(rng, K, N)
+    A[5] = 0.0
+    B[:, 17] = 0.0
+    C = torch.full((M * N,), float("nan"), dtype=torch.float64, device=DEV)
+    # a workspace this small forces column chunks of the B planes
+    rc = slices(colmajor(A), colmajor(B), M, N, K, 1, M, 0, 0, K, 0, 0, 0, 1.0, 0.0, C, M, 0, work_mb=64)
+    assert rc == 0
+    got = C.cpu().numpy().reshape(N, M).T
+    ref = A @ B
+    assert np.all(got[5] == 0.0) and np.all(got[:, 17] == 0.0)
+    assert np.all(np.abs(got - ref) <= 1.5 * _bound(A, B))
