@@ -57,7 +57,7 @@ extern "C" {
                                 projection, leaf, factorization and trace products)
                                 carried out on the BF16 tcgen05 tensor cores as
                                 exact products of 7-bit digit slices with FP32
-                                accumulation (error ~2^-41 of the row/column-scaled
+                                accumulation (error ~2^-46 of the row/column-scaled
                                 bound, FP64-class); small products stay FP64      */
 
 typedef struct hodlr_ctx hodlr_ctx;
@@ -211,8 +211,8 @@ int hodlr_napply(const hodlr_ctx* h, int64_t* out);
  * out[1] = launches, out[2] = algorithmic flops (2 M N K per matrix product),
  * out[3] = algorithmic operand bytes (each of A, B read once and C written once), and per
  * kernel family v (0 SIMT tiles, 1 FP32 large tiles, 2 double-float, 3 narrow products,
- * 4 tcgen05 3xTF32): out[4 + 3v] = milliseconds, out[5 + 3v] = algorithmic flops (useful
- * 2 M N K), out[6 + 3v] = launches; `out` holds 19 doubles.
+ * 4 tcgen05 3xTF32, 5 tcgen05 BF16 digit slices): out[4 + 3v] = milliseconds, out[5 + 3v] =
+ * algorithmic flops (useful 2 M N K), out[6 + 3v] = launches; `out` holds 22 doubles.
  * hodlr_profile(h, 0) stops and clears.  Event pool: 65536 launches.
  * Diagnostics (environment): HODLR_PROFILE_DUMP=<file> makes hodlr_profile_read write one
  * CSV row per GEMM launch (shape, kernel variant, ms); HODLR_TRACE=<file> makes
@@ -243,11 +243,11 @@ int hodlr_peak(int which, double* tflops_out);
  * column-major FP64 device matrices: op(A_b) is M x K (A_b = A + b sA, ld lda, transposed when
  * tA), op(B) is K x N (B_i = B + i sB, ld ldb, transposed when tB), map(b) = b, b^1, b>>1 for
  * bmap = 0, 1, 2, C_b = C + b sC (ld ldc); sA = 0 (sB = 0) shares one A (B) among the batch.
- * Each operand row (A) or column (B) is scaled by a power of two and cut into six balanced 7-bit
- * digits held exactly in BF16; the 21 digit products with p + q <= 5 run on tcgen05 with FP32
- * accumulation in tensor memory, exact for the three leading digit groups over 512-long chunks
- * of K; the result is assembled in 64-bit integers and rounded once.  Error below ~2^-40 of
- * sum_k max_k'|A_ik'| max_k'|B_k'j| (finite inputs).
+ * Each operand row (A) or column (B) is scaled by a power of two and cut into seven balanced
+ * 7-bit digits held exactly in BF16; the 28 digit products with p + q <= 6 run on tcgen05 with
+ * FP32 accumulation in tensor memory, exact for the four leading digit groups over 512-long
+ * chunks of K; the result is assembled in 64-bit integers and rounded once.  Error below
+ * ~2^-46 of sum_k max_k'|A_ik'| max_k'|B_k'j| (finite inputs).
  * work: caller-owned device scratch of work_bytes >= 64 MiB, 256-byte aligned (slice planes and
  * split-K partials; larger problems are processed in batch and column chunks).  cuda_stream may
  * be NULL.  Allocates nothing.  HODLR_ENOMEM if even one product does not fit work_bytes;

@@ -121,7 +121,9 @@ struct Engine : Base {
     g_oz_cfg.split = on && oz ? ozsplit : Scratch{};
   }
   bool graph_mode = false;
-  void set_graph_mode(bool on) override { graph_mode = on; if (on) built = false; }
+  // entering or leaving graph mode invalidates the build: the host copies of the log-det and
+  // the level widths are not refreshed by captured work
+  void set_graph_mode(bool on) override { graph_mode = on; built = false; }
   // tree
   std::vector<std::vector<int>> bnd;     // per depth: node boundaries (2^d + 1)
   int* d_perm_plain = nullptr;           // tree-layout row -> natural index (-1 = padding)
@@ -449,6 +451,13 @@ struct Engine : Base {
     }
   }
 
+  // Products whose accuracy must exceed the digit-slice products' (Gram matrices, whose small
+  // eigenvalues carry the rank decisions and the SMW cores): FP64 FMA even on HODLR_MIXED_BF16
+  struct FP64Only {
+    bool saved;
+    FP64Only() : saved(g_oz_cfg.on) { g_oz_cfg.on = false; }
+    ~FP64Only() { g_oz_cfg.on = saved; }
+  };
   // ---------------------------------------------------------------- GEMM helpers
   void gemmT(GemmArgs g) { gemm<T, T, T, T>(g, scratch, st); }
   // per child block b at depth d: C_b (P x Q) = op(A[b])^T B[b]  (A, B row panels)
@@ -639,6 +648,7 @@ struct Engine : Base {
         g.A = Y; g.lda = N; g.sA = 2 * m; g.tA = 1;
         g.B = Y; g.ldb = N; g.sB = 2 * m;
         g.C = gram; g.ldc = c; g.sC = (long long)c * c; g.batch = np;
+        FP64Only exact;
         g64<T, T>(g);
       }
       pivoted_cholesky<T>(np, c, cap, cap, gram, thr, d_rank[l], d_piv[l], RinvJ, frozen ? 1 : 0, pwork, d_status, st);
@@ -669,6 +679,7 @@ struct Engine : Base {
         g.A = Q1; g.lda = N; g.sA = 2 * m; g.tA = 1;
         g.B = Q1; g.ldb = N; g.sB = 2 * m;
         g.C = gram; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = np;
+        FP64Only exact;
         g64<T, T>(g);
       }
       potrf_lower(np, wl, gram, wl, (long long)wl * wl, d_rank[l], nullptr, d_status, st);
@@ -877,7 +888,7 @@ struct Engine : Base {
   // solve with the block-diagonal of the depth-d subtrees:  out = diag_v(K~_v^{-1}) in
   void solve_depth(const T* in, long long ldi, T* out, long long ldo, int q, int d) {
     const int nl = leaf;
-    if (sizeof(T) == 8) {
+    if (sizeof(T) == 8 && !(oz && g_oz_cfg.on)) {
       leaf_trsm<T, T>(nleaves, nl, Afp, in, ldi, out, ldo, q, st);      // FP64: backward-stable leaf solves
     } else {
       GemmArgs g;                                                      // FP32 bulk: explicit A_b^{-1}
@@ -941,6 +952,17 @@ struct Engine : Base {
   }
   void leaf_solve64(const double* in, long long ldi, double* out, long long ldo, int q) {
     if constexpr (sizeof(T) == 8) {
+      if (oz && g_oz_cfg.on) {
+        // HODLR_MIXED_BF16: the FP64 leaf inverses applied as digit-slice products (error
+        // ~ slicing accuracy x cond(A_b)); the FP64 path keeps the backward-stable substitution
+        GemmArgs g;
+        g.M = leaf; g.N = q; g.K = leaf;
+        g.A = Ainv; g.lda = leaf; g.sA = (long long)leaf * leaf;
+        g.B = in; g.ldb = ldi; g.sB = leaf;
+        g.C = out; g.ldc = ldo; g.sC = leaf; g.batch = nleaves;
+        gemm<double, double, double, double>(g, scratch, st);
+        return;
+      }
       leaf_trsm<double, double>(nleaves, leaf, Afp, in, ldi, out, ldo, q, st);
     } else {
       GemmArgs g;
@@ -1015,6 +1037,7 @@ struct Engine : Base {
         g.A = F[l]; g.lda = N; g.sA = m; g.tA = 1;
         g.B = U[l]; g.ldb = N; g.sB = m;
         g.C = sg; g.ldc = wl; g.sC = (long long)wl * wl; g.batch = 1 << l;
+        FP64Only exact;
         g64<T, double>(g);
       }
       const long long w2 = (long long)wl * wl;
@@ -1261,6 +1284,8 @@ struct Engine : Base {
     if (!built) throw Error(HODLR_EINVAL, "no build");
     derivatives_supported();
     traces_impl(true, t, f);
+    t[0] -= npad;   // padding rows: a unit diagonal, decoupled (see eval)
+    f[0] -= npad;
   }
   // The FP32 sketch of the mixed path carries rounding of relative size 6e-8 into dY, which
   // Alg. 2 multiplies by cond(R) (up to 1/guard = 1e5) in dY R^{-1}; with the bivariate
@@ -2013,21 +2038,21 @@ int hodlr_profile_read(hodlr_ctx* h, double* out) {
   if (!h || !h->e || !out) return HODLR_EINVAL;
   try {
     double ms = 0.0;
-    double per[5][3] = {{0}};   // per kernel family: ms, flops, launches
+    double per[6][3] = {{0}};   // per kernel family: ms, flops, launches
     for (int i = 0; i < g_prof.n; ++i) {
       HODLR_CUDA(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
       float t = 0.f;
       HODLR_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
       ms += t;
       const int* sh = g_prof.shape + 7 * i;
-      const int v = sh[6] >= 10 ? 0 : (sh[6] >= 1 && sh[6] <= 4 ? sh[6] : 0);
+      const int v = sh[6] >= 10 ? 0 : (sh[6] >= 1 && sh[6] <= 5 ? sh[6] : 0);
       per[v][0] += t;
       per[v][1] += 2.0 * (double)sh[0] * sh[1] * sh[2] * sh[3];
       per[v][2] += 1.0;
     }
     out[0] = ms;
     out[1] = g_prof.n;
-    for (int v = 0; v < 5; ++v)
+    for (int v = 0; v < 6; ++v)
       for (int k = 0; k < 3; ++k) out[4 + 3 * v + k] = per[v][k];
     // optional per-launch dump (shape and time) for kernel studies
     if (const char* path = getenv("HODLR_PROFILE_DUMP")) {

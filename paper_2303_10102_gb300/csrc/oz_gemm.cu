@@ -6,28 +6,30 @@
 //   * every row i of A gets an exponent ea_i with max_k |A_ik| < 2^ea_i, every column j of B an
 //     exponent eb_j likewise;
 //   * the scaled row A_ik 2^(6 - ea_i), a number in (-64, 64), is rounded to a fixed-point
-//     integer with 35 fractional bits and cut into S = 6 balanced base-2^7 digits a_p in
+//     integer with 42 fractional bits and cut into S = 7 balanced base-2^7 digits a_p in
 //     [-64, 64]:  A_ik ~ 2^(ea_i - 6) sum_p a_p 2^(-7p); B likewise (digits b_q);
 //   * plane p of A stores a_p 2^(-7p) as BF16 (exact: a digit has at most 7 significant bits),
 //     so that the tensor-core product of planes p and q is sum_k a_p b_q 2^(-7(p+q)), and all
 //     products of one "group" t = p + q are integer multiples of 2^(-7t);
-//   * the products with p + q <= S - 1 are accumulated in FP32 in tensor memory: groups t = 0,
-//     1, 2 in accumulators of their own, whose sums over a 512-long chunk of K stay below 2^23
-//     units and are therefore exact; groups t = 3, 4, 5 share one accumulator (their FP32
-//     rounding is below 2^-45 of the leading group);
-//   * after every chunk the exact group sums are converted to one 64-bit integer per element
-//     (units 2^-14), summed over the chunks exactly, and at the end combined with the tail
-//     group and the scales into the FP64 result (integer arithmetic, one rounding).
-// The dropped groups t >= 6 and the fixed-point rounding bound the error by about 2^-41 of
-// sum_k max_k'|A_ik'| max_k'|B_k'j| -- the accuracy class of double-float arithmetic -- at a
-// cost of 21 BF16 products.
+//   * the products with p + q <= S - 1 are accumulated in FP32 in tensor memory: groups t = 0..3
+//     in accumulators of their own, whose sums over a 512-long chunk of K stay within 2^23 units
+//     and are therefore exact; groups t = 4..6 share one accumulator (scale 2^-28 of the leading
+//     group, so that its FP32 rounding stays near 2^-50 of the result);
+//   * each CTA takes one 512-long chunk of K (longer K is split across CTAs and the FP64
+//     partials are summed in a fixed order); its exact group sums become one 64-bit integer per
+//     element (units 2^-21), which joins the tail group and the scales in integer arithmetic
+//     with one rounding to FP64.
+// The dropped groups t >= 7 and the fixed-point rounding bound the error by about 2^-47 of
+// sum_k max_k'|A_ik'| max_k'|B_k'j| (normwise about 4e-14 on random operands); the FP32
+// accumulation of the tail groups in the tensor cores adds about 2e-13 normwise (measured), at a
+// cost of 28 BF16 products.
 //
-// One CTA (8 warps) computes a 128 x 128 tile of C over a range of K (split across CTAs when the
-// tiles are few): TMA (cp.async.bulk.tensor, 64-byte swizzle) stages 32-wide K slices of all six
-// planes of A and B (96 KB per stage, two stages) behind mbarrier transaction counts; one thread
-// issues the 42 tcgen05.mma (M = 128, N = 128, K = 16) of a slice; the four accumulators fill
-// the 512 TMEM columns; every wait is bounded (a wait that gives up records HODLR_ETIMEOUT,
-// drains what was issued and frees the TMEM).
+// One CTA (8 warps) computes a 128 x 96 tile of C over one chunk of K: TMA
+// (cp.async.bulk.tensor, 64-byte swizzle) stages 32-wide K slices of all seven planes of A and
+// B (98 KB per stage, two stages) behind mbarrier transaction counts; one thread issues the 56
+// tcgen05.mma (M = 128, N = 96, K = 16) of a slice; the five accumulators take 480 of the 512
+// TMEM columns; every wait is bounded (a wait that gives up records HODLR_ETIMEOUT, drains what
+// was issued and frees the TMEM).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -41,14 +43,15 @@
 namespace hodlr {
 namespace {
 
-constexpr int OZ_S = 6;                      // digit planes per operand
+constexpr int OZ_S = 7;                      // digit planes per operand
 constexpr int OZ_NPAIR = OZ_S * (OZ_S + 1) / 2;
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32;
+constexpr int OZ_BM = 128, OZ_BN = 96, OZ_BK = 32;
+constexpr int OZ_NACC = 5;                   // accumulators: groups 0..3 exact, groups 4..5 shared
 constexpr int OZ_KC = 512;                   // exactness chunk of K
 constexpr int OZ_THREADS = 256;
 constexpr int OZ_PLANE_A = OZ_BM * OZ_BK * 2;            // 8 KB per plane and slice
-constexpr int OZ_PLANE_B = OZ_BN * OZ_BK * 2;            // 8 KB
-constexpr int OZ_STAGE = OZ_S * (OZ_PLANE_A + OZ_PLANE_B);   // 96 KB
+constexpr int OZ_PLANE_B = OZ_BN * OZ_BK * 2;            // 6 KB
+constexpr int OZ_STAGE = OZ_S * (OZ_PLANE_A + OZ_PLANE_B);   // 98 KB
 constexpr int OZ_STAGES = 2;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
 constexpr int OZ_WAIT_LIMIT = 1 << 22;
@@ -110,18 +113,16 @@ __device__ __forceinline__ void oz_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void oz_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void oz_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void oz_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive TMEM columns of this thread's lane (no wait: see oz_ld_wait)
+__device__ __forceinline__ void oz_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void oz_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- slicing
 // Operand view: element (b, r, k) at base[b * sb + r * sr + k * sk] (doubles).  The slice planes
@@ -161,19 +162,21 @@ __global__ void oz_rowexp_kernel(OzView v, int* ex) {
   }
 }
 
-// fixed-point value F = round(x 2^(41 - e)) of |x| < 2^e (|F| <= 2^41), by integer operations
+// fixed-point value F = round(x 2^(FB - e)) of |x| < 2^e (|F| <= 2^FB), FB = 6 + 7 (S - 1), by
+// integer operations
+constexpr int OZ_FB = 6 + 7 * (OZ_S - 1);
 __device__ __forceinline__ long long oz_fixed(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int be = (int)((bits >> 52) & 0x7ff);
   if (be == 0 || e <= -1000) return 0;                       // zero or subnormal
   const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);   // x = mant 2^(be - 1075)
-  // F = mant 2^(be - 1075 + 41 - e); the shift is right by sh = e + 1034 - be >= 12
-  const int sh = e + 1034 - be;
+  // F = mant 2^(be - 1075 + FB - e); the shift is right by sh = e + 1075 - FB - be >= 5
+  const int sh = e + 1075 - OZ_FB - be;
   long long f = sh >= 63 ? 0 : ((mant + (1LL << (sh - 1))) >> sh);
   return bits < 0 ? -f : f;
 }
 
-// digits of F: d_0 = round(F 2^-35), then the remainder in base 2^7, balanced (|d| <= 64)
+// digits of F: d_0 = round(F 2^-(FB - 6)), then the remainder in base 2^7, balanced (|d| <= 64)
 __device__ __forceinline__ void oz_digits(long long F, int (&d)[OZ_S]) {
 #pragma unroll
   for (int p = 0; p < OZ_S - 1; ++p) {
@@ -328,9 +331,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int pa = 0; pa < OZ_S; ++pa) {
 #pragma unroll
             for (int pb = 0; pb < OZ_S - pa; ++pb) {
-              const int t = pa + pb, g = t < 3 ? t : 3;
+              const int t = pa + pb, g = t < OZ_NACC - 1 ? t : OZ_NACC - 1;
               // the first product into each accumulator overwrites it
-              const bool first = kt == 0 && kk == 0 && pa == 0 && (g < 3 || t == 3);
+              const bool first = kt == 0 && kk == 0 && pa == 0 && (g < OZ_NACC - 1 || t == OZ_NACC - 1);
               oz_mma(tmem + (uint32_t)(g * OZ_BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
                      oz_desc(oz_smem(planeB(s, pb)) + 32 * kk), idesc, first ? 0u : 1u);
             }
@@ -347,44 +350,42 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_fence_after();
     const int row = m0 + 32 * wq + lane;
     const int ea = row < p.M ? p.exA[(size_t)bA * p.M + row] : 0;
+    const uint32_t lanes = (uint32_t)(32 * wq) << 16;
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t col0 = (uint32_t)(64 * wh + 32 * h);
-      const uint32_t lanes = (uint32_t)(32 * wq) << 16;
-      uint32_t r0[32], r1[32];
-      long long V[32];
+    for (int h = 0; h < 3; ++h) {
+      // warps w and w + 4 take 48 columns each, in pieces of 16
+      const uint32_t col0 = (uint32_t)(48 * wh + 16 * h);
+      uint32_t ra[16], rb[16], rc[16], rd[16], rt[16];
       if (nk > 0) {
-        // groups 0..2 hold exact multiples of 2^(-7g) below 2^(23 - 7g): times 2^14 integers
-        oz_ld32(tmem + lanes + col0, r0);
-        oz_ld32(tmem + lanes + (uint32_t)OZ_BN + col0, r1);
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          V[j] = (long long)(__uint_as_float(r0[j]) * 16384.0f) + (long long)(__uint_as_float(r1[j]) * 16384.0f);
-        oz_ld32(tmem + lanes + (uint32_t)(2 * OZ_BN) + col0, r0);
-        oz_ld32(tmem + lanes + (uint32_t)(3 * OZ_BN) + col0, r1);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) V[j] += (long long)(__uint_as_float(r0[j]) * 16384.0f);
+        oz_ld16(tmem + lanes + col0, ra);
+        oz_ld16(tmem + lanes + (uint32_t)OZ_BN + col0, rb);
+        oz_ld16(tmem + lanes + (uint32_t)(2 * OZ_BN) + col0, rc);
+        oz_ld16(tmem + lanes + (uint32_t)(3 * OZ_BN) + col0, rd);
+        oz_ld16(tmem + lanes + (uint32_t)(4 * OZ_BN) + col0, rt);
+        oz_ld_wait();
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) { V[j] = 0; r1[j] = 0u; }
+        for (int j = 0; j < 16; ++j) ra[j] = rb[j] = rc[j] = rd[j] = rt[j] = 0u;
       }
       if (row >= p.M) continue;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < 16; ++j) {
         const int col = n0 + (int)col0 + j;
         if (col < p.N) {
-          // value = 2^(ea + eb - 12) (V 2^-14 + tail): V (exact, units 2^-14) and the tail group
-          // (FP32, below 2^-21 of the leading groups' scale) join in one 64-bit integer whose
-          // unit 2^-(14 + sh) is as fine as the larger of the two allows
+          // groups 0..3 hold exact multiples of 2^(-7g) below 2^(24 - 7g): times 2^21 integers
+          const float sc = 2097152.0f;
+          const long long Vj = (long long)(__uint_as_float(ra[j]) * sc) + (long long)(__uint_as_float(rb[j]) * sc) +
+                               (long long)(__uint_as_float(rc[j]) * sc) + (long long)(__uint_as_float(rd[j]) * sc);
+          // value = 2^(ea + eb - 12) (V 2^-21 + tail): V and the tail groups (FP32, below 2^-28 of
+          // the leading groups' scale) join in one 64-bit integer of unit 2^-(21 + sh)
           const int eb = p.exB[(size_t)bB * p.N + col];
-          const float tl = __uint_as_float(r1[j]);
-          const long long Vj = V[j];
+          const float tl = __uint_as_float(rt[j]);
           const unsigned long long av = Vj < 0 ? (unsigned long long)(-Vj) : (unsigned long long)Vj;
           int bl = av ? 64 - __clzll((long long)av) : 0;
-          if (tl != 0.0f) bl = max(bl, ilogbf(tl) + 15);
-          const int sh = min(60, 61 - bl);
-          const long long W = (long long)(av << sh) * (Vj < 0 ? -1 : 1) + __float2ll_rn(ldexpf(tl, 14 + sh));
-          const double v = (ea < -1000 || eb < -1000) ? 0.0 : oz_i64_to_f64(W, ea + eb - 12 - 14 - sh);
+          if (tl != 0.0f) bl = max(bl, ilogbf(tl) + 22);
+          const int sh = min(40, 61 - bl);
+          const long long W = (long long)(av << sh) * (Vj < 0 ? -1 : 1) + __float2ll_rn(ldexpf(tl, 21 + sh));
+          const double v = (ea < -1000 || eb < -1000) ? 0.0 : oz_i64_to_f64(W, ea + eb - 12 - 21 - sh);
           if (p.nsplit == 1) {
             double* c = p.C + (size_t)b * p.sC + (size_t)col * p.ldc + row;
             double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);

@@ -281,10 +281,11 @@ class Hodlr:
     def profile(self, enable):
         self._check(self.lib.hodlr_profile(self.h, int(bool(enable))))
 
-    FAMILIES = ("gemm_kernel", "sgemm_large_kernel", "gemm_df_kernel", "gemv_kernel", "tf32x3_gemm_kernel")
+    FAMILIES = ("gemm_kernel", "sgemm_large_kernel", "gemm_df_kernel", "gemv_kernel", "tf32x3_gemm_kernel",
+                "oz_mma_kernel")
 
     def profile_read(self):
-        out = np.zeros(19)
+        out = np.zeros(22)
         self._check(self.lib.hodlr_profile_read(self.h, _dp(out)))
         fam = {name: {"ms": float(out[4 + 3 * v]), "flops": float(out[5 + 3 * v]), "launches": int(out[6 + 3 * v])}
                for v, name in enumerate(self.FAMILIES)}

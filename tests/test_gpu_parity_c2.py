@@ -96,7 +96,7 @@ def test_p2_mixed_frozen_pivots_per_result(p2, point):
     finally:
         h.set_pivots(None)
     e = errors(f, g, np.asarray(F), d)
-    print(f"P2 point {point} frozen pivots: nll {e['nll']:.2e} grad {np.array2string(e['grad'], precision=2)} "
+    print(f"P2 point {point} frozen pivots: nll {e['nll']:.2e} grad {np.array2string(e['grad'], formatter={'float_kind': lambda v: f'{v:.2e}'})} "
           f"fisher max {e['fisher'].max():.2e} eta_g {e['eta_g']:.2e} eta_I {e['eta_I']:.2e}")
     assert e["nll"] <= 1e-6, e
     assert np.all(e["grad"] <= 1e-4), e
@@ -114,7 +114,7 @@ def test_p2_mixed_own_rank_decisions(p2, point):
     diffs = [abs(a - len(J)) for rl, Jl in zip(ranks, d["sets"]) for a, J in zip(rl, Jl)]
     e = errors(f, g, np.asarray(F), d)
     print(f"P2 point {point} own pivots: max rank difference {max(diffs)}, mean {np.mean(diffs):.2f}; "
-          f"nll {e['nll']:.2e} grad {np.array2string(e['grad'], precision=2)} fisher max {e['fisher'].max():.2e} "
+          f"nll {e['nll']:.2e} grad {np.array2string(e['grad'], formatter={'float_kind': lambda v: f'{v:.2e}'})} fisher max {e['fisher'].max():.2e} "
           f"eta_g {e['eta_g']:.2e} eta_I {e['eta_I']:.2e}")
     assert max(diffs) <= 4, diffs
     assert e["nll"] <= 1e-6, e
