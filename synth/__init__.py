@@ -28,7 +28,7 @@ import scipy.fft
 import scipy.linalg
 
 __all__ = ["Workload", "WORKLOADS", "workload", "simulate_y", "batched_draws",
-           "small_workload", "GUARD"]
+           "small_workload", "GUARD", "C3_GUARD"]
 
 # Rank guard of the pivoted QR per arithmetic precision (a block keeps the leading
 # |R_ii| > max(tol, guard) |R_11|).  Alg. 2 multiplies rounding in the kept directions by
@@ -102,6 +102,13 @@ def small_workload(dim=1, G=256, nvar=1, nu=1.5, theta=(1.0, 0.1, 5.0, 1e-4), le
     """A reduced-size workload of the same structure (for parity tests)."""
     return Workload(name, dim, G, nvar, nu, tuple(theta), leaf, cap, c, tol, precision,
                     seed_probe, seed_data)
+
+
+# Rank guard of the batched 1-D workload: with C0's fixed rank 24 and the default guard 1e-5,
+# datasets of more than ~10^4 points drop columns whose summed truncation residual (the leaf
+# extraction adds every block's residual into the leaves) exceeds the nugget, and K~ is not
+# positive definite (17 of the 64 draws); 1e-7 keeps all 64 positive definite.
+C3_GUARD = 1e-7
 
 
 def batched_draws(n_datasets: int = 64, seed: int = 2):
