@@ -46,14 +46,20 @@ namespace {
 constexpr int OZ_S = 7;                      // digit planes per operand
 constexpr int OZ_NPAIR = OZ_S * (OZ_S + 1) / 2;
 constexpr int OZ_BM = 128, OZ_BN = 96, OZ_BK = 32;
-constexpr int OZ_NACC = 5;                   // accumulators: groups 0..3 exact, groups 4..5 shared
+constexpr int OZ_NACC = 5;                   // accumulators: groups 0..3 exact, groups 4..6 shared
 constexpr int OZ_KC = 512;                   // exactness chunk of K
 constexpr int OZ_THREADS = 256;
 constexpr int OZ_PLANE_A = OZ_BM * OZ_BK * 2;            // 8 KB per plane and slice
-constexpr int OZ_PLANE_B = OZ_BN * OZ_BK * 2;            // 6 KB
-constexpr int OZ_STAGE = OZ_S * (OZ_PLANE_A + OZ_PLANE_B);   // 98 KB
-constexpr int OZ_STAGES = 2;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
+// Two tile shapes: 128 x 96 with two 98 KB stages (one CTA per SM, 480 TMEM columns), and for
+// short K (at most four slices) 128 x 32 with one 70 KB stage, so that two CTAs share an SM and
+// one's loads and epilogue overlap the other's products (160 of 256 TMEM columns each); every
+// accumulator starts at a multiple of 32 TMEM columns
+template <int BN, int ST> struct OzTile {
+  static constexpr int PLANE_B = BN * OZ_BK * 2;
+  static constexpr int STAGE = OZ_S * (OZ_PLANE_A + PLANE_B);
+  static constexpr int SMEM = ST * STAGE + 1024 + 256;
+  static constexpr uint32_t TCOLS = OZ_NACC * BN <= 256 ? 256u : 512u;
+};
 constexpr int OZ_WAIT_LIMIT = 1 << 22;
 
 __device__ int g_oz_status;
@@ -123,6 +129,11 @@ __device__ __forceinline__ void oz_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void oz_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void oz_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
 
 // ---------------------------------------------------------------- slicing
 // Operand view: element (b, r, k) at base[b * sb + r * sr + k * sk] (doubles).  The slice planes
@@ -219,12 +230,71 @@ __global__ void oz_slice_kernel(OzView v, const int* ex, __nv_bfloat16* planes, 
   }
 }
 
+// Fused exponent and digit passes.  Rows along k (sk == 1): one warp per row reads it twice (the
+// second read from L1/L2) and writes the planes along k.  Rows along r (sr == 1) with K <= 128: a
+// CTA stages 32 rows x K in shared memory, takes the row maxima there and writes the planes.
+__global__ void oz_slice_rows_kernel(OzView v, int* ex, __nv_bfloat16* planes, int Kp) {
+  const int warps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.y;
+  const int r = blockIdx.x * warps + wid;
+  if (r >= v.R) return;
+  const double* row = v.base + (size_t)b * v.sb + (size_t)r * v.sr;
+  int m = 0;
+  for (int k = lane; k < v.K; k += 32) m = max(m, oz_biased_exp(row[k]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = m == 0 ? -2000 : m - 1023 + 1;
+  if (lane == 0) ex[(size_t)b * v.R + r] = e;
+  const size_t plane = (size_t)v.nb * v.R * Kp;
+  const size_t o0 = ((size_t)b * v.R + r) * Kp;
+  for (int k = lane; k < Kp; k += 32) {
+    int d[OZ_S];
+    oz_digits(oz_fixed(k < v.K ? row[k] : 0.0, e), d);
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) planes[p * plane + o0 + k] = __float2bfloat16_rn(ldexpf((float)d[p], -7 * p));
+  }
+}
+
+__global__ void oz_slice_cols_kernel(OzView v, int* ex, __nv_bfloat16* planes, int Kp) {
+  __shared__ double tile[128][33];   // [k][r]
+  __shared__ int se[32];
+  const int b = blockIdx.y, r0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  const double* base = v.base + (size_t)b * v.sb;
+  for (int k = ty; k < Kp; k += 8) {
+    const int r = r0 + tx;
+    tile[k][tx] = (r < v.R && k < v.K) ? base[(size_t)r * v.sr + (size_t)k * v.sk] : 0.0;
+  }
+  __syncthreads();
+  if (ty == 0) {
+    int m = 0;
+    for (int k = 0; k < v.K; ++k) m = max(m, oz_biased_exp(tile[k][tx]));
+    const int e = m == 0 ? -2000 : m - 1023 + 1;
+    se[tx] = e;
+    if (r0 + tx < v.R) ex[(size_t)b * v.R + r0 + tx] = e;
+  }
+  __syncthreads();
+  const size_t plane = (size_t)v.nb * v.R * Kp;
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + j;
+    if (r >= v.R) continue;
+    const size_t o0 = ((size_t)b * v.R + r) * Kp;
+    for (int k = tx; k < Kp; k += 32) {
+      int d[OZ_S];
+      oz_digits(oz_fixed(tile[k][j], se[j]), d);
+#pragma unroll
+      for (int p = 0; p < OZ_S; ++p) planes[p * plane + o0 + k] = __float2bfloat16_rn(ldexpf((float)d[p], -7 * p));
+    }
+  }
+}
+
 // ---------------------------------------------------------------- the product kernel
 struct OzParams {
   int M, N, K, Kp;          // per product; Kp: padded K of the planes (multiple of 32)
   int nbA, nbB;             // distinct A / B operands (planes per operand: OZ_S)
   int bmap;                 // B operand of product b: b, b^1, b>>1 (or 0 when nbB == 1)
   int nsplit;               // split of K across CTAs: one OZ_KC chunk each
+  int nfast;                // 1: blockIdx.x runs over N tiles (the CTAs that share an A tile run
+                            //    together and read its planes from L2), 0: over M tiles
   const int *exA, *exB;     // exponents [nbA][M], [nbB][N]
   double alpha, beta;
   double* C;                // nsplit == 1: C_b = C + b*sC, leading dimension ldc
@@ -257,15 +327,17 @@ __device__ __forceinline__ double oz_i64_to_f64(long long x, int e2) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFULL)));
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+template <int BN, int ST>
+__global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
     oz_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const OzParams p) {
+  using TL = OzTile<BN, ST>;
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + OZ_STAGES * OZ_STAGE);
-  uint64_t* done = full + OZ_STAGES;
-  uint32_t* tslot = (uint32_t*)(done + OZ_STAGES);
+  uint64_t* full = (uint64_t*)(sm + ST * TL::STAGE);
+  uint64_t* done = full + ST;
+  uint32_t* tslot = (uint32_t*)(done + ST);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  const int m0 = (p.nfast ? blockIdx.y : blockIdx.x) * OZ_BM, n0 = (p.nfast ? blockIdx.x : blockIdx.y) * BN;
   const int b = blockIdx.z / p.nsplit, sp = blockIdx.z % p.nsplit;
   const int bA = p.nbA == 1 ? 0 : b;
   const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
@@ -274,28 +346,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int nk = (kend - kbeg) / OZ_BK;           // slices (kbeg, kend multiples of 32)
 
   if (tid == 0) {
-    for (int s = 0; s < OZ_STAGES; ++s) {
+    for (int s = 0; s < ST; ++s) {
       oz_mbar_init(&full[s], 1);
       oz_mbar_init(&done[s], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(oz_smem(tslot)) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz_smem(tslot)),
+                 "r"(TL::TCOLS)
+                 : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   oz_fence_before();
   __syncthreads();
   oz_fence_after();
   const uint32_t tmem = *tslot;
-  // D FP32; A, B BF16, K-major; N = 128; M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+  // D FP32; A, B BF16, K-major; N = BN; M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(OZ_BM >> 4) << 24);
-  auto planeA = [&](int s, int q) { return sm + s * OZ_STAGE + q * OZ_PLANE_A; };
-  auto planeB = [&](int s, int q) { return sm + s * OZ_STAGE + OZ_S * OZ_PLANE_A + q * OZ_PLANE_B; };
+  auto planeA = [&](int s, int q) { return sm + s * TL::STAGE + q * OZ_PLANE_A; };
+  auto planeB = [&](int s, int q) { return sm + s * TL::STAGE + OZ_S * OZ_PLANE_A + q * TL::PLANE_B; };
   auto issue_loads = [&](int kt) {
-    const int s = kt & 1;
-    oz_expect_tx(&full[s], OZ_STAGE);
+    const int s = kt % ST;
+    oz_expect_tx(&full[s], TL::STAGE);
     const int kx = kbeg + kt * OZ_BK;
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
@@ -307,22 +381,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int wq = warp & 3, wh = warp >> 2;   // TMEM lane quarter and column half of this warp
   bool ok = true;
   int issued = 0, committed = 0;
-  if (tid == 0 && nk > 0) {
-    issue_loads(0);
-    issued = 1;
-  }
   for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt & 1;
-    if (tid == 0 && kt + 1 < nk) {
-      // the other stage was last read by the products of slice kt - 1
-      if (kt >= 1 && !oz_wait(&done[s ^ 1], ((kt - 1) >> 1) & 1)) ok = false;
-      if (ok) {
-        issue_loads(kt + 1);
-        issued = kt + 2;
+    const int s = kt % ST;
+    if (tid == 0) {
+      // keep ST - 1 slices in flight ahead of this one; a stage is reloaded once the products
+      // of its previous slice have completed
+      for (; ok && issued < nk && issued <= kt + ST - 1; ++issued) {
+        if (issued >= ST && !oz_wait(&done[issued % ST], ((issued - ST) / ST) & 1)) {
+          ok = false;
+          break;
+        }
+        issue_loads(issued);
       }
-    }
-    if (tid == 0 && ok) {
-      if (!oz_wait(&full[s], (kt >> 1) & 1)) ok = false;
+      if (ok && !oz_wait(&full[s], (kt / ST) & 1)) ok = false;
       if (ok) {
         oz_fence_after();
 #pragma unroll
@@ -334,7 +405,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const int t = pa + pb, g = t < OZ_NACC - 1 ? t : OZ_NACC - 1;
               // the first product into each accumulator overwrites it
               const bool first = kt == 0 && kk == 0 && pa == 0 && (g < OZ_NACC - 1 || t == OZ_NACC - 1);
-              oz_mma(tmem + (uint32_t)(g * OZ_BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
+              oz_mma(tmem + (uint32_t)(g * BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
                      oz_desc(oz_smem(planeB(s, pb)) + 32 * kk), idesc, first ? 0u : 1u);
             }
           }
@@ -344,7 +415,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   }
-  if (nk > 0 && ok && tid == 0) ok = oz_wait(&done[(nk - 1) & 1], ((nk - 1) >> 1) & 1);
+  if (nk > 0 && ok && tid == 0) ok = oz_wait(&done[(nk - 1) % ST], ((nk - 1) / ST) & 1);
   ok = __syncthreads_and(ok) != 0;
   if (ok) {
     oz_fence_after();
@@ -352,24 +423,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int ea = row < p.M ? p.exA[(size_t)bA * p.M + row] : 0;
     const uint32_t lanes = (uint32_t)(32 * wq) << 16;
 #pragma unroll 1
-    for (int h = 0; h < 3; ++h) {
-      // warps w and w + 4 take 48 columns each, in pieces of 16
-      const uint32_t col0 = (uint32_t)(48 * wh + 16 * h);
-      uint32_t ra[16], rb[16], rc[16], rd[16], rt[16];
+    for (int h = 0; h < BN / 16; ++h) {
+      // warps w and w + 4 take BN / 2 columns each, in pieces of 8
+      const uint32_t col0 = (uint32_t)((BN / 2) * wh + 8 * h);
+      uint32_t ra[8], rb[8], rc[8], rd[8], rt[8];
       if (nk > 0) {
-        oz_ld16(tmem + lanes + col0, ra);
-        oz_ld16(tmem + lanes + (uint32_t)OZ_BN + col0, rb);
-        oz_ld16(tmem + lanes + (uint32_t)(2 * OZ_BN) + col0, rc);
-        oz_ld16(tmem + lanes + (uint32_t)(3 * OZ_BN) + col0, rd);
-        oz_ld16(tmem + lanes + (uint32_t)(4 * OZ_BN) + col0, rt);
+        oz_ld8(tmem + lanes + col0, ra);
+        oz_ld8(tmem + lanes + (uint32_t)BN + col0, rb);
+        oz_ld8(tmem + lanes + (uint32_t)(2 * BN) + col0, rc);
+        oz_ld8(tmem + lanes + (uint32_t)(3 * BN) + col0, rd);
+        oz_ld8(tmem + lanes + (uint32_t)(4 * BN) + col0, rt);
         oz_ld_wait();
       } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) ra[j] = rb[j] = rc[j] = rd[j] = rt[j] = 0u;
+        for (int j = 0; j < 8; ++j) ra[j] = rb[j] = rc[j] = rd[j] = rt[j] = 0u;
       }
       if (row >= p.M) continue;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
+      for (int j = 0; j < 8; ++j) {
         const int col = n0 + (int)col0 + j;
         if (col < p.N) {
           // groups 0..3 hold exact multiples of 2^(-7g) below 2^(24 - 7g): times 2^21 integers
@@ -398,15 +469,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else if (tid == 0) {
+    // give the products and copies already issued a bounded chance to land, then report
     atomicExch(&g_oz_status, HODLR_ETIMEOUT);
-    for (int kt = committed - 1; kt >= 0 && kt >= committed - 2; --kt) oz_wait(&done[kt & 1], (kt >> 1) & 1);
-    for (int kt = issued - 1; kt >= committed && kt >= 0; --kt) oz_wait(&full[kt & 1], (kt >> 1) & 1);
+    for (int kt = committed - 1; kt >= 0 && kt >= committed - ST; --kt) oz_wait(&done[kt % ST], (kt / ST) & 1);
+    for (int kt = issued - 1; kt >= committed && kt >= 0; --kt) oz_wait(&full[kt % ST], (kt / ST) & 1);
   }
   oz_fence_before();
   __syncthreads();
   if (warp == 0) {
     oz_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TL::TCOLS) : "memory");
   }
 }
 
@@ -456,6 +528,18 @@ bool oz_map(CUtensorMap* m, const __nv_bfloat16* planes, int Kp, int R, int npla
 }
 
 void oz_slice(const OzView& v, int Kp, int* ex, __nv_bfloat16* planes, cudaStream_t st) {
+  if (v.sk == 1 && Kp <= 8192) {
+    dim3 g(cdiv(v.R, 8), v.nb);
+    oz_slice_rows_kernel<<<g, 256, 0, st>>>(v, ex, planes, Kp);
+    check_launch("oz_slice_rows");
+    return;
+  }
+  if (v.sr == 1 && Kp <= 128) {
+    dim3 g(cdiv(v.R, 32), v.nb);
+    oz_slice_cols_kernel<<<g, 256, 0, st>>>(v, ex, planes, Kp);
+    check_launch("oz_slice_cols");
+    return;
+  }
   if (v.sk == 1) {
     dim3 g(cdiv(v.R, 8), v.nb);
     oz_rowexp_kernel<<<g, 256, 0, st>>>(v, ex);
@@ -480,9 +564,11 @@ bool oz_eligible(const GemmArgs& g) {
   if (!g_oz_cfg.on || !g_oz_cfg.work.ptr) return false;
   if (g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
   if (g.batch > 65535) return false;
-  // products this small are cheaper on the FP64 pipes than the slicing passes
+  // products this small are cheaper on the FP64 pipes than the slicing passes; narrow sides
+  // (a rank width below the tile) waste tensor-core work but these products are bound by the
+  // FP64 operand traffic, not by the MMAs
   const double mnk = (double)g.M * g.N * g.K * g.batch;
-  return g.M >= 32 && g.N >= 32 && g.K >= 32 && mnk >= (double)(1 << 22);
+  return mnk >= (double)(1 << 22);
 }
 
 // bytes of slicing workspace for a batch of nb products (A and B planes, exponents)
@@ -517,8 +603,38 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
   }
   int nchunk = g.N;
   while (nchunk > OZ_BN && !need(bchunk, nchunk)) nchunk = ((nchunk / 2 + OZ_BN - 1) / OZ_BN) * OZ_BN;
-  if (!need(bchunk, nchunk)) return false;
-  HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  if (!need(bchunk, nchunk)) {
+    // even one product with a 96-column chunk does not fit: split K into ranges (multiples of
+    // the 512-long chunk) whose planes fit, summed into C in FP64 (beta applies to the first)
+    if (Kp <= OZ_KC) return false;
+    const int bmin = paired ? 2 : 1;
+    auto need_k = [&](int kp) {
+      const size_t planes = oz_bytes(sharedA ? 1 : bmin, g.M, nbB_of(bmin), std::min(g.N, OZ_BN), kp);
+      const size_t part = kp > OZ_KC ? (size_t)bmin * g.M * std::min(g.N, OZ_BN) * cdiv(kp, OZ_KC) * 8 : 0;
+      return planes <= w.bytes && part <= split.bytes;
+    };
+    int kr = Kp;
+    while (kr > OZ_KC && !need_k(kr)) kr = cdiv(kr / 2, OZ_KC) * OZ_KC;
+    if (!need_k(kr)) return false;
+    for (int k0 = 0; k0 < g.K; k0 += kr) {
+      GemmArgs h = g;
+      h.K = std::min(kr, g.K - k0);
+      h.A = (const double*)g.A + (g.tA ? (size_t)k0 : (size_t)k0 * g.lda);
+      h.B = (const double*)g.B + (g.tB ? (size_t)k0 * g.ldb : (size_t)k0);
+      if (k0 > 0) h.beta = 1.0;
+      if (!oz_gemm_any(h, split, st)) throw Error(HODLR_ECUDA, "oz_gemm: K range did not fit");
+    }
+    return true;
+  }
+  // short K (one to four 32-wide slices): the two-CTAs-per-SM tile
+  const bool narrow = Kp <= 4 * OZ_BK;
+  constexpr int NBN = 32;
+  using Wide = OzTile<OZ_BN, 2>;
+  using Narrow = OzTile<NBN, 1>;
+  const int bn = narrow ? NBN : OZ_BN;
+  if (narrow) HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<NBN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              Narrow::SMEM));
+  else HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<OZ_BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide::SMEM));
   for (int b0 = 0; b0 < g.batch; b0 += bchunk) {
     const int nb = std::min(bchunk, g.batch - b0);
     const int nbA = sharedA ? 1 : nb, nbB = nbB_of(nb);
@@ -549,7 +665,7 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
       if (g.tB) { vb.sr = 1; vb.sk = g.ldb; } else { vb.sr = g.ldb; vb.sk = 1; }
       oz_slice(vb, Kp, eB, pB, st);
       CUtensorMap mb;
-      if (!oz_map(&mb, pB, Kp, nc, OZ_S * nbB, OZ_BN)) throw Error(HODLR_ECUDA, "oz_gemm: tensor map");
+      if (!oz_map(&mb, pB, Kp, nc, OZ_S * nbB, bn)) throw Error(HODLR_ECUDA, "oz_gemm: tensor map");
       const int nsplit = (int)nsp;
       OzParams p{};
       p.M = g.M; p.N = nc; p.K = g.K; p.Kp = Kp; p.nbA = nbA; p.nbB = nbB;
@@ -558,10 +674,13 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
       p.C = (double*)g.C + (size_t)b0 * g.sC + (size_t)j0 * g.ldc; p.ldc = g.ldc; p.sC = g.sC;
       p.part = (double*)split.ptr;
       if ((long long)nb * nsplit > 65535) throw Error(HODLR_EINVAL, "oz_gemm: batch too large");
-      dim3 grid(cdiv(g.M, OZ_BM), cdiv(nc, OZ_BN), nb * nsplit);
+      // rasterisation: the larger operand's tiles are shared by the CTAs launched together
+      p.nfast = (long long)nbA * g.M > (long long)nbB * nc ? 1 : 0;
+      dim3 grid(p.nfast ? cdiv(nc, bn) : cdiv(g.M, OZ_BM), p.nfast ? cdiv(g.M, OZ_BM) : cdiv(nc, bn), nb * nsplit);
       const bool prof = g_prof.on && g_prof.n < g_prof.cap;
       if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
-      oz_mma_kernel<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, p);
+      if (narrow) oz_mma_kernel<NBN, 1><<<grid, OZ_THREADS, Narrow::SMEM, st>>>(ma, mb, p);
+      else oz_mma_kernel<OZ_BN, 2><<<grid, OZ_THREADS, Wide::SMEM, st>>>(ma, mb, p);
       check_launch("oz_mma_kernel");
       if (prof) {
         cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);

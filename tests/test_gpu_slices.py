@@ -130,3 +130,21 @@ def test_zero_rows_columns_and_chunked_workspace():
     ref = A @ B
     assert np.all(got[5] == 0.0) and np.all(got[:, 17] == 0.0)
     assert np.all(np.abs(got - ref) <= 1.5 * _bound(A, B))
+
+
+def test_long_k_split_into_ranges_and_short_k_tiles():
+    """K = 40000 with a 64 MiB workspace: the operands' planes do not fit at once, so K is cut into
+    ranges whose partial products are summed in FP64; K = 100 takes the 32-column short-K tiles
+    (two CTAs per SM) with a ragged N."""
+    rng = np.random.default_rng(5)
+    for M, N, K in [(130, 130, 40000), (300, 203, 100)]:
+        A = rng.standard_normal((M, K))
+        B = rng.standard_normal((K, N))
+        C = torch.zeros(M * N, dtype=torch.float64, device=DEV)
+        Ast = colmajor(A.T)      # A given transposed (K contiguous), as the Gram products are
+        rc = slices(Ast, colmajor(B), M, N, K, 1, K, 0, 1, K, 0, 0, 0, 1.0, 0.0, C, M, 0, work_mb=64)
+        assert rc == 0
+        got = C.cpu().numpy().reshape(N, M).T
+        ref = A @ B
+        assert np.all(np.abs(got - ref) <= 1.5 * _bound(A, B)), (M, N, K)
+        assert np.linalg.norm(got - ref) <= 5e-13 * np.linalg.norm(ref), (M, N, K)
