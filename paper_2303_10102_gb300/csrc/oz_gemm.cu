@@ -327,6 +327,23 @@ __device__ __forceinline__ double oz_i64_to_f64(long long x, int e2) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFULL)));
 }
 
+// One output element from its five accumulators: groups 0..3 hold exact multiples of 2^(-7g)
+// below 2^(24 - 7g), so their values times 2^(7g) are integers that fit 32 bits; they join in
+// V = sum_g acc_g 2^21 (units 2^-21, |V| < 2^43) and, with the tail groups (FP32, below 2^-28 of
+// the leading scale) in units of 2^-40, in one 64-bit integer W = V 2^19 + round(tail 2^40)
+// (|W| < 2^62), rounded once to FP64 with the scales 2^(ea + eb - 12).
+__device__ __forceinline__ double oz_combine(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t at, int ea,
+                                             int eb) {
+  if (ea < -1000 || eb < -1000) return 0.0;
+  const long long g0 = __float2int_rz(__uint_as_float(a0));
+  const long long g1 = __float2int_rz(__uint_as_float(a1) * 128.0f);
+  const long long g2 = __float2int_rz(__uint_as_float(a2) * 16384.0f);
+  const long long g3 = __float2int_rz(__uint_as_float(a3) * 2097152.0f);
+  const long long V = (g0 << 21) + (g1 << 14) + (g2 << 7) + g3;
+  const long long W = (V << 19) + __float2ll_rn(__uint_as_float(at) * 0x1p40f);
+  return oz_i64_to_f64(W, ea + eb - 12 - 40);
+}
+
 template <int BN, int ST>
 __global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
     oz_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const OzParams p) {
@@ -443,20 +460,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
       for (int j = 0; j < 8; ++j) {
         const int col = n0 + (int)col0 + j;
         if (col < p.N) {
-          // groups 0..3 hold exact multiples of 2^(-7g) below 2^(24 - 7g): times 2^21 integers
-          const float sc = 2097152.0f;
-          const long long Vj = (long long)(__uint_as_float(ra[j]) * sc) + (long long)(__uint_as_float(rb[j]) * sc) +
-                               (long long)(__uint_as_float(rc[j]) * sc) + (long long)(__uint_as_float(rd[j]) * sc);
-          // value = 2^(ea + eb - 12) (V 2^-21 + tail): V and the tail groups (FP32, below 2^-28 of
-          // the leading groups' scale) join in one 64-bit integer of unit 2^-(21 + sh)
-          const int eb = p.exB[(size_t)bB * p.N + col];
-          const float tl = __uint_as_float(rt[j]);
-          const unsigned long long av = Vj < 0 ? (unsigned long long)(-Vj) : (unsigned long long)Vj;
-          int bl = av ? 64 - __clzll((long long)av) : 0;
-          if (tl != 0.0f) bl = max(bl, ilogbf(tl) + 22);
-          const int sh = min(40, 61 - bl);
-          const long long W = (long long)(av << sh) * (Vj < 0 ? -1 : 1) + __float2ll_rn(ldexpf(tl, 21 + sh));
-          const double v = (ea < -1000 || eb < -1000) ? 0.0 : oz_i64_to_f64(W, ea + eb - 12 - 21 - sh);
+          const double v = oz_combine(ra[j], rb[j], rc[j], rd[j], rt[j], ea, p.exB[(size_t)bB * p.N + col]);
           if (p.nsplit == 1) {
             double* c = p.C + (size_t)b * p.sC + (size_t)col * p.ldc + row;
             double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
@@ -483,6 +487,197 @@ __global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
 }
 
 // ordered reduction of the split-K partials (FP64), then alpha / beta
+// ---------------------------------------------------------------- persistent short-K kernel
+// For K <= 128 (at most four 32-wide slices) the product is bound by its FP64 C traffic and by
+// the integer epilogue, and a CTA per tile serialises loads, products and epilogue.  Here one CTA
+// per SM loops over tiles (N tile fastest, so that the CTAs sharing an A tile run together) with
+// three roles:
+//   warp 8 (one thread): TMA loads of the slices into a ring of three 70 KB stages;
+//   warp 9 (one thread): the 56 MMAs of each slice into one of two TMEM accumulator sets;
+//   warps 0..7: the epilogue of the previous tile (warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+//               columns 16 (w / 4) .. + 15, releases the accumulator set, then updates C in FP64).
+// Every wait is bounded; a role whose wait gives up raises an abort flag that stops the others,
+// records HODLR_ETIMEOUT, waits (bounded) for what it issued and lets the CTA free its TMEM.
+constexpr int WS_BN = 32, WS_NST = 3, WS_THREADS = 320;
+constexpr int WS_STAGE = OZ_S * (OZ_PLANE_A + WS_BN * OZ_BK * 2);   // 70 KB
+constexpr int WS_SMEM = WS_NST * WS_STAGE + 1024 + 256;
+
+__device__ __forceinline__ void oz_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    oz_mma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                     const OzParams p, int ntm, int ntn, int ntiles) {
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(sm + WS_NST * WS_STAGE);
+  uint64_t* empty = full + WS_NST;
+  uint64_t* accf = empty + WS_NST;
+  uint64_t* acce = accf + 2;
+  volatile int* abort_flag = (volatile int*)(acce + 2);
+  uint32_t* tslot = (uint32_t*)(acce + 2) + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nk = p.Kp / OZ_BK;                    // 1..4 slices, one K chunk
+  if (tid == 0) {
+    for (int s = 0; s < WS_NST; ++s) {
+      oz_mbar_init(&full[s], 1);
+      oz_mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      oz_mbar_init(&accf[a], 1);
+      oz_mbar_init(&acce[a], 8);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(oz_smem(tslot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  oz_fence_before();
+  __syncthreads();
+  oz_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WS_BN >> 3) << 17) |
+                         ((uint32_t)(OZ_BM >> 4) << 24);
+  auto planeA = [&](int s, int q) { return sm + s * WS_STAGE + q * OZ_PLANE_A; };
+  auto planeB = [&](int s, int q) { return sm + s * WS_STAGE + OZ_S * OZ_PLANE_A + q * (WS_BN * OZ_BK * 2); };
+  auto decode = [&](int t, int& b, int& m0, int& n0) {
+    const int tn = t % ntn, r = t / ntn;
+    m0 = (r % ntm) * OZ_BM;
+    n0 = tn * WS_BN;
+    b = r / ntm;
+  };
+  int issued = 0, committed = 0;   // producer / MMA progress (slices), for the drain after an abort
+  if (warp == 8) {
+    if (lane == 0) {
+      // ---------------- producer
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+        int b, m0, n0;
+        decode(t, b, m0, n0);
+        const int bA = p.nbA == 1 ? 0 : b;
+        const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % WS_NST, u = it / WS_NST;
+          if (u > 0 && !oz_wait(&empty[s], (u - 1) & 1)) { *abort_flag = 1; break; }
+          oz_expect_tx(&full[s], WS_STAGE);
+#pragma unroll
+          for (int q = 0; q < OZ_S; ++q) {
+            oz_tma3(planeA(s, q), &mapA, kt * OZ_BK, m0, q * p.nbA + bA, &full[s]);
+            oz_tma3(planeB(s, q), &mapB, kt * OZ_BK, n0, q * p.nbB + bB, &full[s]);
+          }
+          issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // ---------------- products
+      int it = 0, j = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++j) {
+        const int a = j & 1;
+        if (j >= 2 && !oz_wait(&acce[a], ((j >> 1) - 1) & 1)) { *abort_flag = 1; break; }
+        oz_fence_after();
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % WS_NST;
+          if (!oz_wait(&full[s], (it / WS_NST) & 1)) { ok = false; break; }
+          oz_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+            for (int pa = 0; pa < OZ_S; ++pa) {
+#pragma unroll
+              for (int pb = 0; pb < OZ_S - pa; ++pb) {
+                const int tt = pa + pb, g = tt < OZ_NACC - 1 ? tt : OZ_NACC - 1;
+                const bool first = kt == 0 && kk == 0 && pa == 0 && (g < OZ_NACC - 1 || tt == OZ_NACC - 1);
+                oz_mma(tmem + (uint32_t)(256 * a + g * WS_BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
+                       oz_desc(oz_smem(planeB(s, pb)) + 32 * kk), idesc, first ? 0u : 1u);
+              }
+            }
+          }
+          oz_commit(&empty[s]);
+          committed = it + 1;
+        }
+        if (!ok) { *abort_flag = 1; break; }
+        oz_commit(&accf[a]);
+      }
+    }
+  } else {
+    // ---------------- epilogue
+    const int wq = warp & 3, wh = warp >> 2;
+    const uint32_t lanes = (uint32_t)(32 * wq) << 16;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++j) {
+      const int a = j & 1;
+      bool ok = oz_wait(&accf[a], (j >> 1) & 1);
+      if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; break; }
+      oz_fence_after();
+      int b, m0, n0;
+      decode(t, b, m0, n0);
+      const int bA = p.nbA == 1 ? 0 : b;
+      const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
+      const int row = m0 + 32 * wq + lane;
+      const int c0 = n0 + 16 * wh;
+      const int ea = row < p.M ? p.exA[(size_t)bA * p.M + row] : -2000;
+      double v[16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t ra[8], rb[8], rc[8], rd[8], rt[8];
+        const uint32_t base = tmem + lanes + (uint32_t)(256 * a + 16 * wh + 8 * h);
+        oz_ld8(base, ra);
+        oz_ld8(base + (uint32_t)WS_BN, rb);
+        oz_ld8(base + (uint32_t)(2 * WS_BN), rc);
+        oz_ld8(base + (uint32_t)(3 * WS_BN), rd);
+        oz_ld8(base + (uint32_t)(4 * WS_BN), rt);
+        oz_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int col = c0 + 8 * h + q;
+          const int eb = col < p.N ? p.exB[(size_t)bB * p.N + col] : -2000;
+          v[8 * h + q] = oz_combine(ra[q], rb[q], rc[q], rd[q], rt[q], ea, eb);
+        }
+      }
+      // the accumulator set is free for the tile after next
+      oz_fence_before();
+      __syncwarp();
+      if (lane == 0) oz_arrive(&acce[a]);
+      if (row < p.M) {
+        double* c = p.C + (size_t)b * p.sC + row;
+        double cv[16];
+        if (p.beta != 0.0) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) cv[q] = c0 + q < p.N ? c[(size_t)(c0 + q) * p.ldc] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (c0 + q >= p.N) continue;
+          double out = p.alpha == 1.0 ? v[q] : (p.alpha == -1.0 ? -v[q] : p.alpha * v[q]);
+          if (p.beta != 0.0) out = p.beta == 1.0 ? cv[q] + out : fma(p.beta, cv[q], out);
+          c[(size_t)(c0 + q) * p.ldc] = out;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    // wait (bounded) for the copies and products already issued before the TMEM is freed
+    if (tid == 0) atomicExch(&g_oz_status, HODLR_ETIMEOUT);
+    if (warp == 8 && lane == 0)
+      for (int it = issued - 1; it >= 0 && it >= issued - WS_NST; --it) oz_wait(&full[it % WS_NST], (it / WS_NST) & 1);
+    if (warp == 9 && lane == 0 && committed > 0)
+      oz_wait(&empty[(committed - 1) % WS_NST], ((committed - 1) / WS_NST) & 1);
+  }
+  oz_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    oz_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
 __global__ void oz_reduce_kernel(int M, int N, int nsplit, const double* part, double alpha, double beta, double* C,
                                  long long ldc, long long sC) {
   const int b = blockIdx.y;
@@ -626,14 +821,17 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
     }
     return true;
   }
-  // short K (one to four 32-wide slices): the two-CTAs-per-SM tile
+  // short K (one to four 32-wide slices): the persistent warp-specialised kernel over 128 x 32 tiles
   const bool narrow = Kp <= 4 * OZ_BK;
-  constexpr int NBN = 32;
   using Wide = OzTile<OZ_BN, 2>;
-  using Narrow = OzTile<NBN, 1>;
-  const int bn = narrow ? NBN : OZ_BN;
-  if (narrow) HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<NBN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              Narrow::SMEM));
+  const int bn = narrow ? WS_BN : OZ_BN;
+  static int num_sms = 0;
+  if (!num_sms) {
+    int dev = 0;
+    HODLR_CUDA(cudaGetDevice(&dev));
+    HODLR_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  if (narrow) HODLR_CUDA(cudaFuncSetAttribute(oz_mma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM));
   else HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<OZ_BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide::SMEM));
   for (int b0 = 0; b0 < g.batch; b0 += bchunk) {
     const int nb = std::min(bchunk, g.batch - b0);
@@ -679,9 +877,17 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
       dim3 grid(p.nfast ? cdiv(nc, bn) : cdiv(g.M, OZ_BM), p.nfast ? cdiv(g.M, OZ_BM) : cdiv(nc, bn), nb * nsplit);
       const bool prof = g_prof.on && g_prof.n < g_prof.cap;
       if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
-      if (narrow) oz_mma_kernel<NBN, 1><<<grid, OZ_THREADS, Narrow::SMEM, st>>>(ma, mb, p);
-      else oz_mma_kernel<OZ_BN, 2><<<grid, OZ_THREADS, Wide::SMEM, st>>>(ma, mb, p);
-      check_launch("oz_mma_kernel");
+      if (narrow) {
+        const int ntm = cdiv(g.M, OZ_BM), ntn = cdiv(nc, WS_BN);
+        const long long ntiles = (long long)ntm * ntn * nb;
+        if (ntiles > 0x7fffffffLL) throw Error(HODLR_EINVAL, "oz_gemm: too many tiles");
+        const int ctas = (int)std::min<long long>(ntiles, num_sms);
+        oz_mma_ws_kernel<<<ctas, WS_THREADS, WS_SMEM, st>>>(ma, mb, p, ntm, ntn, (int)ntiles);
+        check_launch("oz_mma_ws_kernel");
+      } else {
+        oz_mma_kernel<OZ_BN, 2><<<grid, OZ_THREADS, Wide::SMEM, st>>>(ma, mb, p);
+        check_launch("oz_mma_kernel");
+      }
       if (prof) {
         cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
         if (g_prof.shape) {
