@@ -1838,17 +1838,23 @@ void batch_capture(hodlr_ctx* const* hs, int nb, const double* thetas, const dou
   };
   const long long k0 = g_kernel_launches;
   cudaGraph_t graph = nullptr;
+  // branches: datasets are dealt round-robin to nbr streams (each runs its datasets one after
+  // another), so that independent evaluations overlap without flooding the GPU with streams
+  int nbr = std::min(nb, 8);
+  if (const char* v = getenv("HODLR_BATCH_BRANCHES")) nbr = std::max(1, std::min(nb, atoi(v)));
   HODLR_CUDA(cudaStreamBeginCapture(B.root, cudaStreamCaptureModeRelaxed));
   try {
     HODLR_CUDA(cudaEventRecord(B.ev[0], B.root));
+    for (int k = 0; k < nbr; ++k) HODLR_CUDA(cudaStreamWaitEvent(B.br[k], B.ev[0], 0));
     for (int i = 0; i < nb; ++i) {
-      HODLR_CUDA(cudaStreamWaitEvent(B.br[i], B.ev[0], 0));
-      hs[i]->e->set_stream(B.br[i]);
+      hs[i]->e->set_stream(B.br[i % nbr]);
       hs[i]->e->oz_enter(true);
       hs[i]->e->eval_graph(thetas + 4 * (size_t)i, ys[i]);
       hs[i]->e->oz_enter(false);
-      HODLR_CUDA(cudaEventRecord(B.ev[1 + i], B.br[i]));
-      HODLR_CUDA(cudaStreamWaitEvent(B.root, B.ev[1 + i], 0));
+    }
+    for (int k = 0; k < nbr; ++k) {
+      HODLR_CUDA(cudaEventRecord(B.ev[1 + k], B.br[k]));
+      HODLR_CUDA(cudaStreamWaitEvent(B.root, B.ev[1 + k], 0));
     }
   } catch (...) {
     cudaStreamEndCapture(B.root, &graph);

@@ -23,23 +23,33 @@ from .lib import HodlrError
 
 
 def mle_bfgs(ctx, y, theta0, rtol=1e-6, max_iter=200, freeze_pivots=True, history=None):
-    """Minimise NLL~(theta) from theta0 by BFGS in u = log theta.
+    """Minimise NLL~(theta) from theta0 by BFGS.
 
-    Returns (theta_hat, info): info = {"nll", "grad", "fisher", "iterations", "converged",
-    "message"}, the gradient and Fisher matrix evaluated at theta_hat.  With freeze_pivots the
-    context keeps the start point's pivot sets afterwards (call ctx.set_pivots(None) to release
-    them).  Points where K~ is not positive definite (HODLR_ENOTPD) count as +inf, which makes
-    the line search step back."""
+    The variables are whitened log-parameters u = C^T (log theta - log theta0), with C C^T the
+    Fisher information in log coordinates at theta0 (J I(theta0) J, J = diag(theta0)), so that the
+    Hessian of the NLL in u is close to the identity: the four parameters differ by orders of
+    magnitude in scale and curvature.  Returns (theta_hat, info) with info = {"nll", "grad",
+    "fisher", "iterations", "converged", "message"}, the gradient and Fisher matrix evaluated at
+    theta_hat.  With freeze_pivots the context keeps the start point's pivot sets afterwards (call
+    ctx.set_pivots(None) to release them).  Points where K~ is not positive definite
+    (HODLR_ENOTPD) count as +inf, which makes the line search step back."""
     from scipy.optimize import minimize
 
     theta0 = np.asarray(theta0, dtype=np.float64)
     if freeze_pivots:
         ctx.build(theta0)
         ctx.set_pivots(ctx.get_pivots())
+    _, _, F0 = ctx.eval(theta0, y)
+    J = np.diag(theta0)
+    C = np.linalg.cholesky(J @ np.asarray(F0) @ J)       # log coordinates, whitened
+    Cinv_T = np.linalg.inv(C).T
     cache = {}
 
+    def theta_of(u):
+        return theta0 * np.exp(Cinv_T @ u)
+
     def fun(u):
-        th = np.exp(u)
+        th = theta_of(u)
         key = tuple(th)
         if key not in cache:
             try:
@@ -49,16 +59,17 @@ def mle_bfgs(ctx, y, theta0, rtol=1e-6, max_iter=200, freeze_pivots=True, histor
                     raise
                 cache[key] = (np.inf, np.zeros(4))
             else:
-                cache[key] = (f, np.asarray(g) * th)      # d/du = theta * d/dtheta
+                # d/du = C^{-1} (theta * d/dtheta)
+                cache[key] = (f, np.linalg.solve(C, np.asarray(g) * th))
             if history is not None:
                 history.append({"theta": th.tolist(), "nll": cache[key][0]})
         return cache[key]
 
-    # BFGS stops on a small gradient (gtol, in log-parameter units) or on a relative step below
-    # rtol (xrtol)
-    res = minimize(fun, np.log(theta0), jac=True, method="BFGS",
-                   options={"gtol": 1e-8, "xrtol": rtol, "maxiter": max_iter})
-    theta = np.exp(res.x)
+    # in whitened coordinates a unit step is one standard error: stop when the gradient is below
+    # rtol of that scale or the relative step is below rtol
+    res = minimize(fun, np.zeros(4), jac=True, method="BFGS",
+                   options={"gtol": rtol, "xrtol": rtol, "maxiter": max_iter})
+    theta = theta_of(res.x)
     f, g, F = ctx.eval(theta, y)
     return theta, {"nll": float(f), "grad": np.asarray(g).tolist(), "fisher": np.asarray(F).tolist(),
                    "iterations": int(res.nit), "converged": bool(res.success), "message": str(res.message)}
