@@ -267,6 +267,7 @@ struct Engine : Base {
     }
     // physics geometry
     ph.dim = dim; ph.G = G; ph.nvar = nvar; ph.nu = nu; ph.h = 1.0 / (G + 1);
+    ph.df_fft = oz ? 1 : 0;   // HODLR_MIXED_BF16: FFT butterflies of the FP64 fields in double-float
     int L = 1;
     while (L < 2 * G - 1) L <<= 1;
     ph.L = L; ph.L1 = 0; ph.L2 = 0;

@@ -160,6 +160,7 @@ struct PhysicsDesc {
   double nu, h;
   int L;          // FFT embedding length per axis (power of two >= 2G-1)
   int L1, L2;     // four-step split of a 1-D embedding longer than 4096 (L = L1*L2)
+  int df_fft = 0; // FP64 fields: FFT butterflies in double-float arithmetic (FP32 pipes)
 };
 // Philox probe panel R^(level): N x ncols in tree order; row i non-zero iff it lies in the
 // right child of its level pair (right_child[i] = level mask bit).  The counter of row i is

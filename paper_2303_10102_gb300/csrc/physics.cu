@@ -24,6 +24,49 @@ template <class T> struct CT;
 template <> struct CT<float> { using C = float2; };
 template <> struct CT<double> { using C = double2; };
 
+// Double-float arithmetic for the FFT passes of FP64 fields on the mixed BF16 path: a value is an
+// unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits).  Sums use the
+// two-sum error-free transformation, products the FMA-based two-product; both renormalise.
+// GB300 runs FP32 operations at about seventy times its FP64 rate, so the butterflies are cheaper
+// this way although each takes several FP32 operations.  Values enter from and leave to FP64
+// storage (the passes exchange FP64 data through global memory).
+struct dfl {
+  float hi, lo;
+  __device__ __forceinline__ dfl() {}
+  __device__ __forceinline__ dfl(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ dfl(double d) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+  }
+  __device__ __forceinline__ operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ dfl df_renorm(float s, float e) {
+  const float h = s + e;
+  return dfl(h, e - (h - s));
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  const float s = a.hi + b.hi, bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + dfl(-b.hi, -b.lo); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return df_renorm(p, e);
+}
+__device__ __forceinline__ dfl operator*(dfl a, double b) { return a * dfl(b); }
+struct dcx {
+  dfl x, y;
+  __device__ __forceinline__ dcx() {}
+  __device__ __forceinline__ dcx(dfl a, dfl b) : x(a), y(b) {}
+  __device__ __forceinline__ dcx(double2 v) : x(v.x), y(v.y) {}
+  __device__ __forceinline__ operator double2() const { return make_double2((double)x, (double)y); }
+};
+struct DFA {};   // arithmetic tag: FP64 storage, double-float arithmetic
+template <> struct CT<DFA> { using C = dcx; };
+
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
 template <class C> __device__ __forceinline__ C cmul(C a, C b) {
@@ -177,9 +220,9 @@ __device__ void dit(C* x, int L, int nl, const C* tw) {
     __syncthreads();
   }
 }
-template <class C>
-__device__ void load_tw(C* s, const C* g, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = g[i];
+template <class C, class G>
+__device__ void load_tw(C* s, const G* g, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = C(g[i]);
   __syncthreads();
 }
 
@@ -197,11 +240,11 @@ __device__ __forceinline__ typename CT<T>::C twiddle_L(long long e, int L) {  //
 // ---------------------------------------------------------------- 1-D, L <= 4096, one line per CTA
 // MODE 0: convolution (forward, multiply by lam0 [and lam1], inverse) of a pair of real columns.
 // MODE 1: forward transform of a real sequence `in` (length L), lam0 = Re(X) * scale.
-template <class T, int MODE>
+template <class T, int MODE, class A = T>
 __global__ void fft1_small_kernel(int L, int Ns, int ncols, const T* in, long long ldi, T* lam0,
                                   const T* lam1, T* out0, T* out1, long long ldo, const typename CT<T>::C* twg,
                                   double scale) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L / 2;
@@ -251,10 +294,10 @@ __global__ void fft1_small_kernel(int L, int Ns, int ncols, const T* in, long lo
 // Pass A: for NV consecutive i2 (lines), DIF over i1 (stride L2), then multiply by W_L^{i2*k1}.
 //   src: real pair columns (ncols, ld) [MODE 0] or real sequence of length L [MODE 1];
 //   dst: complex W[f][k*L2 + i2].
-template <class T, int MODE>
+template <class T, int MODE, class A = T>
 __global__ void fft1_passA_kernel(int L1, int L2, int logL1, int Ns, int ncols, const T* in, long long ldi,
                                   typename CT<T>::C* W, const typename CT<T>::C* twg, int nv) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L1 / 2;
@@ -276,20 +319,20 @@ __global__ void fft1_passA_kernel(int L1, int L2, int logL1, int Ns, int ncols, 
   }
   __syncthreads();
   dif(x, L1, nv, tw);
-  C* Wf = W + (size_t)f * L;
+  typename CT<T>::C* Wf = W + (size_t)f * L;
   for (int e = threadIdx.x; e < L1 * nv; e += blockDim.x) {
     int v = e % nv, k = e / nv;
     int i2 = i2b + v;
     long long k1 = bitrev(k, logL1);
-    Wf[(size_t)k * L2 + i2] = cmul(x[k * nv + v], twiddle_L<T>(k1 * i2, L));
+    Wf[(size_t)k * L2 + i2] = cmul(x[k * nv + v], C(twiddle_L<T>(k1 * i2, L)));
   }
 }
 // Pass B: per line k (contiguous L2): MODE 0: DIF, multiply lam0 [lam1], DIT (in place to W / W2);
 // MODE 1: DIF only, lam0 = Re * scale.
-template <class T, int MODE>
+template <class T, int MODE, class A = T>
 __global__ void fft1_passB_kernel(int L1, int L2, typename CT<T>::C* W, typename CT<T>::C* W2, T* lam0,
                                   const T* lam1, const typename CT<T>::C* twg, double scale) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L2 / 2;
@@ -297,7 +340,7 @@ __global__ void fft1_passB_kernel(int L1, int L2, typename CT<T>::C* W, typename
   load_tw(tw, twg, L2 / 2);
   const int k = blockIdx.x, f = blockIdx.y;
   const int L = L1 * L2;
-  C* line = W + (size_t)f * L + (size_t)k * L2;
+  typename CT<T>::C* line = W + (size_t)f * L + (size_t)k * L2;
   for (int i = threadIdx.x; i < L2; i += blockDim.x) x[i] = line[i];
   __syncthreads();
   dif(x, L2, 1, tw);
@@ -316,15 +359,15 @@ __global__ void fft1_passB_kernel(int L1, int L2, typename CT<T>::C* W, typename
   for (int i = threadIdx.x; i < L2; i += blockDim.x) line[i] = x[i];
   if (lam1) {
     dit(y, L2, 1, tw);
-    C* line2 = W2 + (size_t)f * L + (size_t)k * L2;
+    typename CT<T>::C* line2 = W2 + (size_t)f * L + (size_t)k * L2;
     for (int i = threadIdx.x; i < L2; i += blockDim.x) line2[i] = y[i];
   }
 }
 // Pass C: multiply by conj W_L^{i2*k1}, DIT over i1, write real pair columns (i < Ns).
-template <class T>
+template <class T, class A = T>
 __global__ void fft1_passC_kernel(int L1, int L2, int logL1, int Ns, int ncols, const typename CT<T>::C* W,
                                   T* out, long long ldo, const typename CT<T>::C* twg, int nv) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L1 / 2;
@@ -333,7 +376,7 @@ __global__ void fft1_passC_kernel(int L1, int L2, int logL1, int Ns, int ncols, 
   const int f = blockIdx.y;
   const int i2b = blockIdx.x * nv;
   const int c0 = 2 * f, c1 = 2 * f + 1;
-  const C* Wf = W + (size_t)f * L;
+  const typename CT<T>::C* Wf = W + (size_t)f * L;
   for (int e = threadIdx.x; e < L1 * nv; e += blockDim.x) {
     int v = e % nv, k = e / nv;
     int i2 = i2b + v;
@@ -355,10 +398,10 @@ __global__ void fft1_passC_kernel(int L1, int L2, int logL1, int Ns, int ncols, 
 // ---------------------------------------------------------------- 2-D (L x L embedding of a G x G grid)
 // Row pass forward: line = row y of field f; input real pair columns (natural p = y*G + x), or the
 // L x L real embedding (MODE 1, all L rows).  Output W[f][y][k] (rows y < nrows).
-template <class T, int MODE>
+template <class T, int MODE, class A = T>
 __global__ void fft2_rows_fwd_kernel(int L, int G, int ncols, const T* in, long long ldi, typename CT<T>::C* W,
                                      const typename CT<T>::C* twg) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L / 2;
@@ -378,23 +421,23 @@ __global__ void fft2_rows_fwd_kernel(int L, int G, int ncols, const T* in, long 
   }
   __syncthreads();
   dif(x, L, 1, tw);
-  C* row = W + ((size_t)f * nrows + y) * L;
+  typename CT<T>::C* row = W + ((size_t)f * nrows + y) * L;
   for (int i = threadIdx.x; i < L; i += blockDim.x) row[i] = x[i];
 }
 // Column pass: NV adjacent columns k of field f; rows y < nin loaded (rest zero).
 // MODE 0: DIF, multiply by lam0 [lam1], DIT, store rows y < G into W [W2].
 // MODE 1: DIF only, lam0[ky*L + k] = Re * scale (spectrum).
-template <class T, int MODE>
+template <class T, int MODE, class A = T>
 __global__ void fft2_cols_kernel(int L, int nin, typename CT<T>::C* W, typename CT<T>::C* W2, T* lam0,
                                  const T* lam1, const typename CT<T>::C* twg, int nv, double scale, int nout) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L / 2;
   C* y = x + (size_t)L * nv;
   load_tw(tw, twg, L / 2);
   const int kb = blockIdx.x * nv, f = blockIdx.y;
-  C* Wf = W + (size_t)f * nin * L;
+  typename CT<T>::C* Wf = W + (size_t)f * nin * L;
   for (int e = threadIdx.x; e < L * nv; e += blockDim.x) {
     int v = e % nv, r = e / nv;
     C val = {T(0), T(0)};
@@ -425,7 +468,7 @@ __global__ void fft2_cols_kernel(int L, int nin, typename CT<T>::C* W, typename 
   }
   if (lam1) {
     dit(y, L, nv, tw);
-    C* W2f = W2 + (size_t)f * nin * L;
+    typename CT<T>::C* W2f = W2 + (size_t)f * nin * L;
     for (int e = threadIdx.x; e < nout * nv; e += blockDim.x) {
       int v = e % nv, r = e / nv;
       W2f[(size_t)r * L + kb + v] = y[r * nv + v];
@@ -433,17 +476,17 @@ __global__ void fft2_cols_kernel(int L, int nin, typename CT<T>::C* W, typename 
   }
 }
 // Row pass inverse: DIT along x for rows y < G, write x < G into real pair columns.
-template <class T>
+template <class T, class A = T>
 __global__ void fft2_rows_inv_kernel(int L, int G, int ncols, const typename CT<T>::C* W, T* out, long long ldo,
                                      const typename CT<T>::C* twg) {
-  using C = typename CT<T>::C;
+  using C = typename CT<A>::C;
   extern __shared__ unsigned char sm[];
   C* tw = (C*)sm;
   C* x = tw + L / 2;
   load_tw(tw, twg, L / 2);
   const int y = blockIdx.x, f = blockIdx.y;
   const int c0 = 2 * f, c1 = 2 * f + 1;
-  const C* row = W + ((size_t)f * G + y) * L;
+  const typename CT<T>::C* row = W + ((size_t)f * G + y) * L;
   for (int i = threadIdx.x; i < L; i += blockDim.x) x[i] = row[i];
   __syncthreads();
   dit(x, L, 1, tw);
@@ -833,8 +876,8 @@ template void matern_spectra<double>(const PhysicsDesc&, double, double, double*
 template void matern_spectra<float>(const PhysicsDesc&, double, double, float*, float*, void*, const float*,
                                     cudaStream_t);
 
-template <class T>
-void fft_convolve(const PhysicsDesc& p, int ncols, const T* in, long long ldi, const T* lam0, const T* lam1, T* out0,
+template <class T, class A>
+void fft_convolve_impl(const PhysicsDesc& p, int ncols, const T* in, long long ldi, const T* lam0, const T* lam1, T* out0,
                   T* out1, long long ldo, void* work, const T* tw, cudaStream_t st) {
   using C = typename CT<T>::C;
   if (ncols <= 0) return;
@@ -843,8 +886,8 @@ void fft_convolve(const PhysicsDesc& p, int ncols, const T* in, long long ldi, c
   const int Ns = p.dim == 1 ? p.G : p.G * p.G;
   if (p.dim == 1 && p.L1 == 0) {
     size_t sm = (p.L / 2 + 2 * (size_t)p.L) * sizeof(C);
-    set_smem(fft1_small_kernel<T, 0>, sm);
-    fft1_small_kernel<T, 0><<<nf, 256, sm, st>>>(p.L, Ns, ncols, in, ldi, (T*)lam0, lam1, out0, out1, ldo, twc, 1.0);
+    set_smem(fft1_small_kernel<T, 0, A>, sm);
+    fft1_small_kernel<T, 0, A><<<nf, 256, sm, st>>>(p.L, Ns, ncols, in, ldi, (T*)lam0, lam1, out0, out1, ldo, twc, 1.0);
     check_launch("fft1_small");
     return;
   }
@@ -854,42 +897,53 @@ void fft_convolve(const PhysicsDesc& p, int ncols, const T* in, long long ldi, c
   if (p.dim == 1) {
     int nv = 16;
     size_t smA = (p.L1 / 2 + (size_t)p.L1 * nv) * sizeof(C);
-    set_smem(fft1_passA_kernel<T, 0>, smA);
-    fft1_passA_kernel<T, 0><<<dim3(p.L2 / nv, nf), 256, smA, st>>>(p.L1, p.L2, ilog2(p.L1), Ns, ncols, in, ldi, W,
+    set_smem(fft1_passA_kernel<T, 0, A>, smA);
+    fft1_passA_kernel<T, 0, A><<<dim3(p.L2 / nv, nf), 256, smA, st>>>(p.L1, p.L2, ilog2(p.L1), Ns, ncols, in, ldi, W,
                                                                     twc, nv);
     check_launch("fft1_passA");
     size_t smB = (p.L2 / 2 + 2 * (size_t)p.L2) * sizeof(C);
-    set_smem(fft1_passB_kernel<T, 0>, smB);
-    fft1_passB_kernel<T, 0><<<dim3(p.L1, nf), 256, smB, st>>>(p.L1, p.L2, W, W2, (T*)lam0, lam1, twc + p.L1 / 2, 1.0);
+    set_smem(fft1_passB_kernel<T, 0, A>, smB);
+    fft1_passB_kernel<T, 0, A><<<dim3(p.L1, nf), 256, smB, st>>>(p.L1, p.L2, W, W2, (T*)lam0, lam1, twc + p.L1 / 2, 1.0);
     check_launch("fft1_passB");
     size_t smC = smA;
-    set_smem(fft1_passC_kernel<T>, smC);
-    fft1_passC_kernel<T><<<dim3(p.L2 / nv, nf), 256, smC, st>>>(p.L1, p.L2, ilog2(p.L1), Ns, ncols, W, out0, ldo,
+    set_smem(fft1_passC_kernel<T, A>, smC);
+    fft1_passC_kernel<T, A><<<dim3(p.L2 / nv, nf), 256, smC, st>>>(p.L1, p.L2, ilog2(p.L1), Ns, ncols, W, out0, ldo,
                                                                   twc, nv);
     check_launch("fft1_passC");
     if (lam1) {
-      fft1_passC_kernel<T><<<dim3(p.L2 / nv, nf), 256, smC, st>>>(p.L1, p.L2, ilog2(p.L1), Ns, ncols, W2, out1,
+      fft1_passC_kernel<T, A><<<dim3(p.L2 / nv, nf), 256, smC, st>>>(p.L1, p.L2, ilog2(p.L1), Ns, ncols, W2, out1,
                                                                     ldo, twc, nv);
       check_launch("fft1_passC");
     }
     return;
   }
   size_t smR = (p.L / 2 + (size_t)p.L) * sizeof(C);
-  set_smem(fft2_rows_fwd_kernel<T, 0>, smR);
-  fft2_rows_fwd_kernel<T, 0><<<dim3(p.G, nf), 256, smR, st>>>(p.L, p.G, ncols, in, ldi, W, twc);
+  set_smem(fft2_rows_fwd_kernel<T, 0, A>, smR);
+  fft2_rows_fwd_kernel<T, 0, A><<<dim3(p.G, nf), 256, smR, st>>>(p.L, p.G, ncols, in, ldi, W, twc);
   check_launch("fft2_rows_fwd");
   int nv = sizeof(T) == 8 ? 2 : 4;
   size_t smC = (p.L / 2 + 2 * (size_t)p.L * nv) * sizeof(C);
-  set_smem(fft2_cols_kernel<T, 0>, smC);
-  fft2_cols_kernel<T, 0><<<dim3(p.L / nv, nf), 256, smC, st>>>(p.L, p.G, W, W2, (T*)lam0, lam1, twc, nv, 1.0, p.G);
+  set_smem(fft2_cols_kernel<T, 0, A>, smC);
+  fft2_cols_kernel<T, 0, A><<<dim3(p.L / nv, nf), 256, smC, st>>>(p.L, p.G, W, W2, (T*)lam0, lam1, twc, nv, 1.0, p.G);
   check_launch("fft2_cols");
-  set_smem(fft2_rows_inv_kernel<T>, smR);
-  fft2_rows_inv_kernel<T><<<dim3(p.G, nf), 256, smR, st>>>(p.L, p.G, ncols, W, out0, ldo, twc);
+  set_smem(fft2_rows_inv_kernel<T, A>, smR);
+  fft2_rows_inv_kernel<T, A><<<dim3(p.G, nf), 256, smR, st>>>(p.L, p.G, ncols, W, out0, ldo, twc);
   check_launch("fft2_rows_inv");
   if (lam1) {
-    fft2_rows_inv_kernel<T><<<dim3(p.G, nf), 256, smR, st>>>(p.L, p.G, ncols, W2, out1, ldo, twc);
+    fft2_rows_inv_kernel<T, A><<<dim3(p.G, nf), 256, smR, st>>>(p.L, p.G, ncols, W2, out1, ldo, twc);
     check_launch("fft2_rows_inv");
   }
+}
+template <class T>
+void fft_convolve(const PhysicsDesc& p, int ncols, const T* in, long long ldi, const T* lam0, const T* lam1, T* out0,
+                  T* out1, long long ldo, void* work, const T* tw, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (p.df_fft) {
+      fft_convolve_impl<T, DFA>(p, ncols, in, ldi, lam0, lam1, out0, out1, ldo, work, tw, st);
+      return;
+    }
+  }
+  fft_convolve_impl<T, T>(p, ncols, in, ldi, lam0, lam1, out0, out1, ldo, work, tw, st);
 }
 template void fft_convolve<double>(const PhysicsDesc&, int, const double*, long long, const double*, const double*,
                                    double*, double*, long long, void*, const double*, cudaStream_t);

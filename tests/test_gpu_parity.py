@@ -86,6 +86,21 @@ def test_tree_probe_and_physics(name):
         assert rel(Y, m.apply(X, w.theta, which)) < 1e-11, which
 
 
+@pytest.mark.parametrize("name", ["1d-uni", "2d-uni", "2d-biv", "1d-uneven", "1d-long"])
+def test_bf16_path_physics_products(name):
+    """Physics products of the mixed BF16 path (FP64 fields; FFT butterflies in double-float,
+    DST products as BF16 digit slices) against the FP64 oracle.  "1d-long" has a 16384-point
+    embedding, which takes the four-step FFT passes."""
+    w = SMALL[name] if name in SMALL else synth.small_workload(dim=1, G=8192, nvar=1, nu=1.5,
+                                                               theta=(1.0, 0.1, 5.0, 1e-3), leaf=64, cap=12, c=12)
+    h = ctx(w, "bf16")
+    m = Model(w.dim, w.G, w.nvar, w.nu)
+    X = np.random.default_rng(7).standard_normal((h.N, 5))
+    for which in PARAMS + ("K",):
+        Y = h.apply(w.theta, which, X).cpu().numpy()
+        assert rel(Y, m.apply(X, w.theta, which)) < 1e-11, which
+
+
 @pytest.mark.parametrize("nvar", [1, 2])
 def test_fp32_physics_products_2d(nvar):
     """FP32 physics products on a 128 x 128 grid, where the DST products of the operator solve
