@@ -291,16 +291,31 @@ def roofline_entry(prof, ms_step, steps, pk, prec, live_peaks=None):
     fd = fams[dom]
     achieved = fd["flops"] / (fd["ms"] / 1000.0) / 1e12 if fd["ms"] > 0 else 0.0
     meas = live_peaks or {}
-    if dom == "oz_mma_kernel":
-        # 28 BF16 digit products per FP64-class multiply-add: the FP64-equivalent peak is the
-        # measured BF16 tensor peak / 28
-        peak_v = pk["bf16_tflops"] / 28.0
-        note = ("measured bf16 burst peak (MEASURED_PEAKS.json) / 28 digit products per FP64-class product; "
+    bf16 = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])   # kernels timed inside a long step
+    if dom in ("oz_mma_kernel", "oz_atb_kernel", "oz_ab_kernel"):
+        # 28 BF16 digit products per FP64-class multiply-add: the tensor-pipe time is 28 x the
+        # useful 2MNK at the measured BF16 peak; the HBM time is the FP64 operand bytes (A and B
+        # read once, C read when beta != 0 and written) at the measured copy bandwidth.  The
+        # roofline is the larger of the two.
+        sec = fd["ms"] / 1000.0
+        t_tensor = 28.0 * fd["flops"] / (bf16 * 1e12)
+        t_hbm = fd.get("bytes", 0.0) / (pk["hbm_gbs"] * 1e9)
+        if t_hbm > t_tensor and sec > 0:
+            return {"bound": "hbm", "kernel": dom, "achieved": fd["bytes"] / sec / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "frac": t_hbm / sec, "traffic": None,
+                    "peak_source": ("measured copy bandwidth (MEASURED_PEAKS.json); achieved counts the FP64 operand "
+                                    "bytes of the products (A, B once; C read and written) (of measured)"),
+                    "tensor_frac": t_tensor / sec,
+                    "kernel_share_of_step": fd["ms"] / steps / ms_step if ms_step else None,
+                    "launches": fd["launches"] // max(steps, 1),
+                    "families_ms_per_step": {k: v["ms"] / steps for k, v in fams.items()}}
+        peak_v = bf16 / 28.0
+        note = ("measured bf16 sustained peak (MEASURED_PEAKS.json) / 28 digit products per FP64-class product; "
                 "achieved counts the useful 2MNK of the FP64 products")
         bound = "tensor"
     elif dom == "tf32x3_gemm_kernel":
-        peak_v = pk["bf16_tflops"] * TF32_PER_BF16 / 3.0
-        note = "measured bf16 burst peak x nominal TF32/BF16 ratio (1.1/2.25) / 3 products (3xTF32)"
+        peak_v = bf16 * TF32_PER_BF16 / 3.0
+        note = "measured bf16 sustained peak x nominal TF32/BF16 ratio (1.1/2.25) / 3 products (3xTF32)"
         bound = "tensor"
     elif dom == "gemm_df_kernel":
         peak_v = meas.get("fp32_ffma_tflops", 77.9) / DF_INSTR_PER_MAC

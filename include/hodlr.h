@@ -211,8 +211,10 @@ int hodlr_napply(const hodlr_ctx* h, int64_t* out);
  * out[1] = launches, out[2] = algorithmic flops (2 M N K per matrix product),
  * out[3] = algorithmic operand bytes (each of A, B read once and C written once), and per
  * kernel family v (0 SIMT tiles, 1 FP32 large tiles, 2 double-float, 3 narrow products,
- * 4 tcgen05 3xTF32, 5 tcgen05 BF16 digit slices): out[4 + 3v] = milliseconds, out[5 + 3v] =
- * algorithmic flops (useful 2 M N K), out[6 + 3v] = launches; `out` holds 22 doubles.
+ * 4 tcgen05 3xTF32, 5 tcgen05 BF16 digit slices from sliced planes, 6 fused long-K digit
+ * slices, 7 fused short-K digit slices): out[4 + 4v] = milliseconds, out[5 + 4v] =
+ * algorithmic flops (useful 2 M N K), out[6 + 4v] = launches, out[7 + 4v] = algorithmic
+ * operand bytes; `out` holds 36 doubles.
  * hodlr_profile(h, 0) stops and clears.  Event pool: 65536 launches.
  * Diagnostics (environment): HODLR_PROFILE_DUMP=<file> makes hodlr_profile_read write one
  * CSV row per GEMM launch (shape, kernel variant, ms); HODLR_TRACE=<file> makes

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhodlr.so")
-UNITS = ["gemm.cu", "small.cu", "physics.cu", "hodlr.cu", "noalloc.cu", "tc_gemm.cu", "peaks.cu", "oz_gemm.cu"]
+UNITS = ["gemm.cu", "small.cu", "physics.cu", "hodlr.cu", "noalloc.cu", "tc_gemm.cu", "peaks.cu", "oz_gemm.cu", "tree.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-diag-suppress", "177,128"]

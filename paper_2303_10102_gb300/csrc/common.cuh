@@ -31,9 +31,17 @@ struct GemmProfile {
   cudaEvent_t* ev = nullptr;   // 2 per launch
   int cap = 0, n = 0;
   double flops = 0.0, bytes = 0.0;
+  double fbytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // algorithmic operand bytes per kernel family
   int* shape = nullptr;        // per launch: M, N, K, batch, tA, tB, kernel variant
 };
 extern GemmProfile g_prof;
+// kernel family of a recorded variant (0 SIMT tiles incl. split-K variants 10 * nsplit, 1 FP32
+// large tiles, 2 double-float, 3 narrow, 4 tcgen05 3xTF32, 5..7 tcgen05 BF16 digit slices)
+inline int prof_family(int variant) { return variant >= 10 ? 0 : (variant >= 1 && variant <= 7 ? variant : 0); }
+inline void prof_add_bytes(int variant, double b) {
+  g_prof.bytes += b;
+  g_prof.fbytes[prof_family(variant)] += b;
+}
 
 // Optional launch timeline (HODLR_TRACE): an event after every launch on the traced stream;
 // the interval between consecutive events is charged to the launch that ends it (idle gaps

@@ -300,8 +300,8 @@ bool gemv_narrow(const GemmArgs& g, cudaStream_t st) {
     }
     ++g_prof.n;
     g_prof.flops += 2.0 * (double)g.M * g.N * g.K * g.batch;
-    g_prof.bytes += ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
-                     (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch;
+    prof_add_bytes(3, ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
+                     (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch);
   }
   return true;
 }
@@ -343,8 +343,8 @@ void gemm_tiles(const GemmArgs& g, Scratch s, cudaStream_t st) {
     ++g_prof.n;
     double mnk = (double)g.M * g.N * g.K * g.batch;
     g_prof.flops += 2.0 * mnk;
-    g_prof.bytes += ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
-                     (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch;
+    prof_add_bytes(10 * nsplit, ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
+                     (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch);
   }
   if (nsplit > 1) {
     long long mn = (long long)g.M * g.N;
@@ -598,6 +598,8 @@ void gemm_df_tiles(const GemmArgs& g, Scratch s, cudaStream_t st) {
     }
     ++g_prof.n;
     g_prof.flops += 2.0 * (double)g.M * g.N * g.K * g.batch;
+    prof_add_bytes(2, ((double)g.M * g.K * sizeof(TA) + (double)g.K * g.N * sizeof(TB) +
+                       (double)g.M * g.N * sizeof(TC) * (g.beta != 0.0 ? 2 : 1)) * g.batch);
   }
   if (nsplit > 1) {
     long long mn = (long long)g.M * g.N;
@@ -748,8 +750,8 @@ bool sgemm_large(const GemmArgs& g, cudaStream_t st) {
     }
     ++g_prof.n;
     g_prof.flops += 2.0 * (double)g.M * g.N * g.K * g.batch;
-    g_prof.bytes += ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N * (g.beta != 0.0 ? 2 : 1)) * 4.0 *
-                    g.batch;
+    prof_add_bytes(1, ((double)g.M * g.K + (double)g.K * g.N + (double)g.M * g.N * (g.beta != 0.0 ? 2 : 1)) * 4.0 *
+                    g.batch);
   }
   return true;
 }

@@ -69,6 +69,7 @@ struct Base {
   virtual void logdet_levels(double* out) = 0;
   virtual void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) = 0;
   virtual void get_pivots(int32_t* piv) const = 0;
+  virtual void read_perm(int64_t* perm) = 0;   // real tree position -> natural index, from the device maps
   virtual cudaStream_t stream() const = 0;
   // Capture-safe evaluation (NLL and gradient) for CUDA-graph batching: no host
   // synchronisation, static level widths (the rank cap), statuses left on the device; the
@@ -88,11 +89,18 @@ struct Base {
   // are padding rows, which every panel keeps at zero and K~ keeps decoupled (unit diagonal).
   int N = 0, Nr = 0, tau = 0, leaf = 0, c = 0, cap = 0, nleaves = 0;
   int npad = 0;                              // padding rows (N - Nr)
-  std::vector<int64_t> perm64;               // real tree position -> natural index (Nr)
-  std::vector<int> permpad;                  // tree-layout row -> natural index, -1 = padding (N)
-  std::vector<int> rowid;                    // tree-layout row -> real tree position, -1 = padding
-  std::vector<int> real2pad;                 // real tree position -> tree-layout row (Nr)
+  TreeDesc td{};                             // cluster tree (the order itself is made on the device)
   std::vector<int> leafreal;                 // real rows per leaf slot
+  // real tree position -> natural index (Nr), by the closed forms of the tree order on the host
+  // (planning query only: an engine's device maps come from the tree_order kernel)
+  void plan_perm(int64_t* perm) const {
+    for (int p = 0; p < td.Ns; ++p) {
+      const int s = tree_spatial_pos(td, p);
+      int lo, hi;
+      tree_leaf(td, s, lo, hi);
+      for (int v = 0; v < td.nvar; ++v) perm[td.nvar * lo + v * (hi - lo) + (s - lo)] = (int64_t)v * td.Ns + p;
+    }
+  }
   std::vector<std::vector<int>> host_rank;   // per level
   long long napply = 0;
   double logdet = 0.0;
@@ -224,47 +232,8 @@ struct Engine : Base {
     bnd.assign(tau + 1, {});
     for (int d = 0; d <= tau; ++d)
       for (int q = 0; q <= (1 << d); ++q) bnd[d].push_back((q << (tau - d)) * this->leaf);
-    // spatial order
-    std::vector<int> sp(Ns);
-    if (dim == 1) {
-      for (int i = 0; i < Ns; ++i) sp[i] = i;
-    } else {
-      std::vector<std::pair<long long, int>> key(Ns);
-      int nbits = 1;
-      while ((1 << nbits) < G) ++nbits;
-      for (int p = 0; p < Ns; ++p) {
-        int ix = p % G, iy = p / G;
-        long long k = 0;
-        for (int b = 0; b < nbits; ++b) {
-          k |= (long long)((ix >> b) & 1) << (2 * b);
-          k |= (long long)((iy >> b) & 1) << (2 * b + 1);
-        }
-        key[p] = {k, p};
-      }
-      std::stable_sort(key.begin(), key.end(), [](auto& a, auto& b) { return a.first < b.first; });
-      for (int i = 0; i < Ns; ++i) sp[i] = key[i].second;
-    }
-    // real tree order: within a leaf, [variable 1 of its points, variable 2 of the same points]
-    perm64.assign(Nr, 0);
-    permpad.assign(N, -1);
-    rowid.assign(N, -1);
-    real2pad.assign(Nr, 0);
-    leafreal.assign(nleaves, 0);
-    {
-      int pos = 0;
-      for (int b = 0; b < nleaves; ++b) {
-        const int lo = sb[tau][b], hi = sb[tau][b + 1], s0 = b * this->leaf;
-        int k = 0;
-        for (int v = 0; v < nvar; ++v)
-          for (int i = lo; i < hi; ++i, ++k, ++pos) {
-            perm64[pos] = v * Ns + sp[i];
-            permpad[s0 + k] = (int)perm64[pos];
-            rowid[s0 + k] = pos;
-            real2pad[pos] = s0 + k;
-          }
-        leafreal[b] = k;
-      }
-    }
+    for (int b = 0; b < nleaves; ++b) leafreal.push_back(nvar * (sb[tau][b + 1] - sb[tau][b]));
+    td.dim = dim; td.G = G; td.nvar = nvar; td.Ns = Ns; td.tau = tau; td.slot = this->leaf;
     // physics geometry
     ph.dim = dim; ph.G = G; ph.nvar = nvar; ph.nu = nu; ph.h = 1.0 / (G + 1);
     ph.df_fft = oz ? 1 : 0;   // HODLR_MIXED_BF16: FFT butterflies of the FP64 fields in double-float
@@ -407,29 +376,15 @@ struct Engine : Base {
   }
 
   void upload_tree() {
-    HODLR_CUDA(cudaMemcpyAsync(d_perm_plain, permpad.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
-    HODLR_CUDA(cudaMemcpyAsync(d_real2pad, real2pad.data(), Nr * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (d_rowid) HODLR_CUDA(cudaMemcpyAsync(d_rowid, rowid.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    tree_order(td, N, d_perm_plain, d_rowid, d_real2pad, st);
     HODLR_CUDA(cudaMemcpyAsync(d_leafreal, leafreal.data(), nleaves * sizeof(int), cudaMemcpyHostToDevice, st));
     upload_phys(P);
     if (P64.perm) upload_phys(P64);
-    for (int l = 1; l <= tau; ++l) {
-      std::vector<unsigned char> m(N, 0);
-      const auto& b = bnd[l];
-      for (size_t q = 1; q + 1 < b.size(); q += 2)
-        for (int i = b[q]; i < b[q + 1]; ++i) m[i] = rowid[i] >= 0 ? 1 : 0;
-      HODLR_CUDA(cudaMemcpyAsync(d_mask[l], m.data(), N, cudaMemcpyHostToDevice, st));
-      HODLR_CUDA(cudaStreamSynchronize(st));
-    }
+    for (int l = 1; l <= tau; ++l) tree_level_mask(N, msize(l), d_rowid, d_mask[l], st);
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
   template <class V> void upload_phys(Phys<V>& Q) {
-    std::vector<int> pv(N);
-    for (int i = 0; i < N; ++i) {
-      const int n = permpad[i];
-      pv[i] = n < 0 ? -1 : (nvar == 1 ? n : (n % Ns) + (n / Ns) * (Ns * Q.qc));
-    }
-    HODLR_CUDA(cudaMemcpyAsync(Q.perm, pv.data(), N * sizeof(int), cudaMemcpyHostToDevice, st));
+    tree_phys_perm(d_perm_plain, N, Ns, nvar, Q.qc, Q.perm, st);
     if (dim == 2) dst_matrix<V>(G, Q.S, st);
     if (Q.Shi) tf32_split((const float*)Q.S, Q.Shi, Q.Slo, (long long)G * G, st);
     if (Q.Sdf) df_split((const double*)Q.S, Q.Sdf, (long long)G * G, st);
@@ -1497,6 +1452,16 @@ struct Engine : Base {
     frozen = true;
     built = false;
   }
+  void read_perm(int64_t* perm) override {
+    std::vector<int> pp(N), rid(d_rowid ? N : 0);
+    HODLR_CUDA(cudaMemcpyAsync(pp.data(), d_perm_plain, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, st));
+    if (d_rowid) HODLR_CUDA(cudaMemcpyAsync(rid.data(), d_rowid, sizeof(int) * (size_t)N, cudaMemcpyDeviceToHost, st));
+    HODLR_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < N; ++i) {
+      const int pos = d_rowid ? rid[i] : i;
+      if (pos >= 0) perm[pos] = pp[i];
+    }
+  }
   void get_pivots(int32_t* piv) const override {
     size_t off = 0;
     for (int l = 1; l <= tau; ++l) {
@@ -1713,7 +1678,7 @@ int hodlr_plan(const hodlr_model* m, const hodlr_opts* o, int64_t* dims_out, int
     std::unique_ptr<Base> b(make_engine(m, o, nullptr));
     dims_out[0] = b->Nr; dims_out[1] = b->tau; dims_out[2] = b->leaf; dims_out[3] = b->c; dims_out[4] = b->cap;
     dims_out[5] = b->nleaves;
-    if (perm_out) std::memcpy(perm_out, b->perm64.data(), sizeof(int64_t) * b->Nr);
+    if (perm_out) b->plan_perm(perm_out);
   } catch (const Error& x) {
     return x.code;
   } catch (const std::bad_alloc&) {
@@ -1941,7 +1906,11 @@ int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, con
 }
 int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out) {
   if (!h || !h->e || !perm_out) return HODLR_EINVAL;
-  std::memcpy(perm_out, h->e->perm64.data(), sizeof(int64_t) * h->e->Nr);
+  try {
+    h->e->read_perm(perm_out);
+  } catch (const Error& x) {
+    return x.code;
+  }
   return HODLR_OK;
 }
 int hodlr_dims(const hodlr_ctx* h, int64_t* out) {
@@ -2018,6 +1987,7 @@ int hodlr_profile(hodlr_ctx* h, int enable) {
     }
     g_prof.n = 0;
     g_prof.flops = g_prof.bytes = 0.0;
+    for (double& b : g_prof.fbytes) b = 0.0;
     g_prof.on = enable != 0;
     g_trace.on = false;
     if (enable && getenv("HODLR_TRACE")) {
@@ -2045,22 +2015,24 @@ int hodlr_profile_read(hodlr_ctx* h, double* out) {
   if (!h || !h->e || !out) return HODLR_EINVAL;
   try {
     double ms = 0.0;
-    double per[6][3] = {{0}};   // per kernel family: ms, flops, launches
+    double per[8][3] = {{0}};   // per kernel family: ms, flops, launches
     for (int i = 0; i < g_prof.n; ++i) {
       HODLR_CUDA(cudaEventSynchronize(g_prof.ev[2 * i + 1]));
       float t = 0.f;
       HODLR_CUDA(cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]));
       ms += t;
       const int* sh = g_prof.shape + 7 * i;
-      const int v = sh[6] >= 10 ? 0 : (sh[6] >= 1 && sh[6] <= 5 ? sh[6] : 0);
+      const int v = prof_family(sh[6]);
       per[v][0] += t;
       per[v][1] += 2.0 * (double)sh[0] * sh[1] * sh[2] * sh[3];
       per[v][2] += 1.0;
     }
     out[0] = ms;
     out[1] = g_prof.n;
-    for (int v = 0; v < 6; ++v)
-      for (int k = 0; k < 3; ++k) out[4 + 3 * v + k] = per[v][k];
+    for (int v = 0; v < 8; ++v) {
+      for (int k = 0; k < 3; ++k) out[4 + 4 * v + k] = per[v][k];
+      out[7 + 4 * v] = g_prof.fbytes[v];
+    }
     // optional per-launch dump (shape and time) for kernel studies
     if (const char* path = getenv("HODLR_PROFILE_DUMP")) {
       if (FILE* f = fopen(path, "w")) {

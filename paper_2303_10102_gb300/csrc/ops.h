@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "tree.cuh"
+
 namespace hodlr {
 
 struct Scratch {
@@ -85,6 +87,15 @@ template <class TS, class TD> void convert(const TS* src, TD* dst, long long n, 
 template <class T> void fill(T* p, T v, long long n, cudaStream_t st);
 // dst[i + j*ldd] = src[perm[i] + j*lds] (gather rows), or scatter when `scatter`:
 // dst[perm[i] + j*ldd] = src[i + j*lds]; optional alpha*src + beta*dst2 for scatter_axpy.
+// cluster-tree order on the device (tree.cu): permpad[N] tree-layout row -> natural index (-1 on
+// padding rows), rowid[N] (may be null) tree-layout row -> real tree position (-1 on padding),
+// real2pad[Nr] real tree position -> tree-layout row
+void tree_order(const TreeDesc& t, int N, int* permpad, int* rowid, int* real2pad, cudaStream_t st);
+// tree-layout row -> row of a physics panel with variable blocks of Ns x qc (-1 on padding)
+void tree_phys_perm(const int* permpad, int N, int Ns, int nvar, int qc, int* out, cudaStream_t st);
+// rows of the right children of the level whose nodes are msize rows (real rows only)
+void tree_level_mask(int N, int msize, const int* rowid, unsigned char* mask, cudaStream_t st);
+
 template <class TS, class TD>
 void permute_rows(const TS* src, long long lds, TD* dst, long long ldd, const int* perm, int n,
                   int ncols, int scatter, cudaStream_t st);

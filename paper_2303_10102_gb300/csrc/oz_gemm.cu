@@ -486,7 +486,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
   }
 }
 
-// ordered reduction of the split-K partials (FP64), then alpha / beta
 // ---------------------------------------------------------------- persistent short-K kernel
 // For K <= 128 (at most four 32-wide slices) the product is bound by its FP64 C traffic and by
 // the integer epilogue, and a CTA per tile serialises loads, products and epilogue.  Here one CTA
@@ -678,6 +677,558 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- fused digit production
+// The two kernels below read the FP64 operands themselves and store the digit planes straight
+// into shared memory, in the layout the TMA loads give (K-major rows of 64 bytes; the 16-byte
+// chunk c of row r sits at chunk c ^ ((r >> 1) & 3), the 64-byte swizzle), so that the planes
+// never pass through HBM.  The exponents come from a pass of their own (oz_exp_chunks_kernel):
+// one per row over the whole K of a short product, one per row and 512-long chunk of K for a
+// long one (each chunk's exact group sums are scaled by its own exponents).
+
+// Balanced digits by one biased addition: with C' = 64 sum_{p=1..6} 2^(7(6-p)),
+// F + C' = d_0 2^42 + sum_{p=1..6} u_p 2^(7(6-p)), u_p in [0, 127], so that d_0 in [-64, 64] and
+// d_p = u_p - 64 in [-64, 63] (|F| <= 2^48).  A digit becomes the FP32 value d 2^(-7p) through a
+// float whose exponent field carries the scale: (2^(23-7p) + u 2^(-7p)) - (2^(23-7p) + 64 2^(-7p)),
+// exact, and exact again as BF16 (at most seven significant bits).
+constexpr long long OZ_CLOW =
+    64LL * ((1LL << 35) + (1LL << 28) + (1LL << 21) + (1LL << 14) + (1LL << 7) + 1LL);
+
+__device__ __forceinline__ float oz_dig_f(uint32_t u, int p) {
+  const uint32_t ef = (uint32_t)(150 - 7 * p) << 23;
+  return __uint_as_float(ef | u) - __uint_as_float(ef | 64u);
+}
+__device__ __forceinline__ void oz_digits_f(double x, int e, float (&f)[OZ_S]) {
+  const long long G = oz_fixed(x, e) + OZ_CLOW;
+  const uint32_t hi = (uint32_t)((unsigned long long)G >> 32), lo = (uint32_t)G;
+  f[0] = oz_dig_f((uint32_t)((int)(G >> 42) + 64), 0);
+  f[1] = oz_dig_f((hi >> 3) & 127u, 1);
+  f[2] = oz_dig_f(__funnelshift_r(lo, hi, 28) & 127u, 2);
+  f[3] = oz_dig_f((lo >> 21) & 127u, 3);
+  f[4] = oz_dig_f((lo >> 14) & 127u, 4);
+  f[5] = oz_dig_f((lo >> 7) & 127u, 5);
+  f[6] = oz_dig_f(lo & 127u, 6);
+}
+// digits of 8 consecutive values of row r (k = 8q .. 8q + 7 of a 32-wide slice) into the 16-byte
+// chunk q of that row in each of the seven planes (plane p at slice0 + p * pstride)
+__device__ __forceinline__ void oz_put8(const double (&x)[8], int e, unsigned char* slice0, int r, int q,
+                                        int pstride) {
+  uint32_t w[OZ_S][4];
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    float fa[OZ_S], fb[OZ_S];
+    oz_digits_f(x[i], e, fa);
+    oz_digits_f(x[i + 1], e, fb);
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(fa[p], fb[p]);
+      w[p][i >> 1] = *reinterpret_cast<uint32_t*>(&h);
+    }
+  }
+  const int off = r * 64 + ((q ^ ((r >> 1) & 3)) << 4);
+#pragma unroll
+  for (int p = 0; p < OZ_S; ++p)
+    *reinterpret_cast<uint4*>(slice0 + p * pstride + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+__device__ __forceinline__ void oz_fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// exponent of every row over chunks of `chunk` values of k: ex[(b * nch + c) * R + r]
+__global__ void oz_exp_chunks_kernel(OzView v, int chunk, int nch, int* ex) {
+  const int b = blockIdx.z, c = blockIdx.y;
+  const double* base = v.base + (size_t)b * v.sb;
+  const int k0 = c * chunk, k1 = min(v.K, k0 + chunk);
+  int m = 0, r;
+  if (v.sk == 1) {   // a warp per row, along k
+    const int lane = threadIdx.x & 31;
+    r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= v.R) return;
+    const double* row = base + (size_t)r * v.sr;
+    for (int k = k0 + lane; k < k1; k += 32) m = max(m, oz_biased_exp(__ldg(row + k)));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane) return;
+  } else {           // a thread per row, threads on consecutive rows
+    r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= v.R) return;
+    for (int k = k0; k < k1; ++k) m = max(m, oz_biased_exp(__ldg(base + (size_t)r * v.sr + (size_t)k * v.sk)));
+  }
+  ex[((size_t)b * nch + c) * v.R + r] = m == 0 ? -2000 : m - 1023 + 1;
+}
+
+// ---------------------------------------------------------------- fused long-K products
+// C_b = alpha op(A_b) op(B_b) + beta C_b where the rows of op(A) and the columns of op(B) are
+// contiguous along K (A^T B of column-major operands: the Gram and projection products of the
+// sketch), M <= 128, K long.  A CTA takes BN columns of one product over a range of 512-long
+// chunks of K:
+//   warps 5..12 (producers): read 32-wide slices of the M rows of op(A) and the BN columns of
+//       op(B) in FP64, cut them into digits with the chunk's exponents and store the 14 planes
+//       of the slice into one of two shared-memory stages;
+//   warp 4 (one thread): the 56 MMAs of each slice into a TMEM accumulator set (two sets used
+//       alternately per chunk when they fit in the 512 columns, else one);
+//   warps 0..3: after each chunk, the integer epilogue of its accumulators (TMEM lane quarter
+//       w) added in FP64 to the CTA's running sums in shared memory; at the end the sums go to
+//       C (a single K range) or to the split-K partials.
+// Two tiles: AR = 128 rows of A planes with BN = 48 (two accumulator sets), and for M <= 64,
+// AR = 64 with BN = 80 (one set): the MMA still reads 128 rows, the upper 64 from whatever
+// follows the plane in shared memory, which reaches only rows of D that are never read.  So do
+// the unwritten rows beyond M and columns beyond N.  Every wait is bounded (abort flag, status
+// HODLR_ETIMEOUT, drain of the issued MMAs before the TMEM is freed).
+constexpr int AT_NPROD = 8;
+constexpr int AT_THREADS = 32 * (5 + AT_NPROD);
+template <int AR, int BN> struct AtTile {
+  static constexpr int PLANE_A = AR * 64;                      // bytes per plane and slice
+  static constexpr int PLANE_B = BN * 64;
+  static constexpr int STAGE = OZ_S * (PLANE_A + PLANE_B);
+  static constexpr int SUMS = AR * BN * 8;
+  static constexpr int SMEM = 2 * STAGE + SUMS + 1024 + 256;
+  static constexpr int NSETS = 2 * OZ_NACC * BN <= 512 ? 2 : 1;
+  static constexpr int SETW = NSETS == 2 ? 256 : 0;            // TMEM columns between sets
+};
+
+struct AtParams {
+  const double *A, *B;     // row i of op(A_b): A + bA sA + i lda; column j of op(B_b): B + bB sB + j ldb
+  long long lda, sA, ldb, sB;
+  int M, N, K, nbA, nbB, bmap;
+  int nch, cpr, nrange;    // 512-long chunks of K; chunks per range; ranges (split of K across CTAs)
+  const int *exA, *exB;    // [nbA][nch][M], [nbB][nch][N]
+  double alpha, beta;
+  double* C;
+  long long ldc, sC;
+  double* part;            // nrange > 1: partials ((b * nrange + range) * M * N) + i + j * M
+};
+
+template <int AR, int BN>
+__global__ void __launch_bounds__(AT_THREADS, 1) oz_atb_kernel(const AtParams p) {
+  using TL = AtTile<AR, BN>;
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  double* sums = (double*)(sm + 2 * TL::STAGE);   // [column][AR rows]
+  uint64_t* full = (uint64_t*)(sm + 2 * TL::STAGE + TL::SUMS);
+  uint64_t* empty = full + 2;
+  uint64_t* accf = empty + 2;
+  uint64_t* acce = accf + 2;
+  volatile int* abort_flag = (volatile int*)(acce + 2);
+  uint32_t* tslot = (uint32_t*)(acce + 2) + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int part = blockIdx.x, range = blockIdx.y, b = blockIdx.z;
+  const int bA = p.nbA == 1 ? 0 : b;
+  const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
+  const int n0 = part * BN, nv = min(BN, p.N - n0);
+  const int c0 = range * p.cpr, c1 = min(p.nch, c0 + p.cpr);
+  const int Kp = ((p.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  const int nsl = (min(c1 * OZ_KC, Kp) - c0 * OZ_KC) / OZ_BK;   // 32-wide slices of this range
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      oz_mbar_init(&full[s], AT_NPROD);
+      oz_mbar_init(&empty[s], 1);
+      oz_mbar_init(&accf[s], 1);
+      oz_mbar_init(&acce[s], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(oz_smem(tslot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int i = tid; i < AR * BN; i += AT_THREADS) sums[i] = 0.0;
+  oz_fence_before();
+  __syncthreads();
+  oz_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(OZ_BM >> 4) << 24);
+  int committed = 0;   // MMA progress (slices), for the drain after an abort
+  if (warp >= 5) {
+    // ---------------- producers
+    const int ptid = tid - 5 * 32;
+    const double* Ab = p.A + (size_t)bA * p.sA;
+    const double* Bb = p.B + (size_t)bB * p.sB + (size_t)n0 * p.ldb;
+    const int tasks = (p.M + nv) * 4;
+    for (int s = 0; s < nsl; ++s) {
+      if (__any_sync(0xffffffffu, *abort_flag)) break;
+      const int st = s & 1, u = s >> 1;
+      if (u > 0) {
+        const bool ok = oz_wait(&empty[st], (u - 1) & 1);
+        if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; break; }
+      }
+      const int ks = c0 * (OZ_KC / OZ_BK) + s, ch = ks / (OZ_KC / OZ_BK), kb = ks * OZ_BK;
+      unsigned char* stg = sm + st * TL::STAGE;
+      for (int t = ptid; t < tasks; t += 32 * AT_NPROD) {
+        const int rho = t >> 2, q = t & 3;   // four threads per row: 256 contiguous bytes
+        const double* src;
+        int e, r, pstride;
+        unsigned char* slice0;
+        if (rho < p.M) {
+          src = Ab + (size_t)rho * p.lda;
+          e = __ldg(p.exA + ((size_t)bA * p.nch + ch) * p.M + rho);
+          slice0 = stg; r = rho; pstride = TL::PLANE_A;
+        } else {
+          r = rho - p.M;
+          src = Bb + (size_t)r * p.ldb;
+          e = __ldg(p.exB + ((size_t)bB * p.nch + ch) * p.N + n0 + r);
+          slice0 = stg + OZ_S * TL::PLANE_A; pstride = TL::PLANE_B;
+        }
+        const int k = kb + 8 * q;
+        double x[8];
+        if (k + 8 <= p.K && (((uintptr_t)(src + k)) & 15) == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(src + k + i));
+            x[i] = v.x; x[i + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) x[i] = k + i < p.K ? __ldg(src + k + i) : 0.0;
+        }
+        oz_put8(x, e, slice0, r, q, pstride);
+      }
+      oz_fence_async_smem();
+      __syncwarp();
+      if (lane == 0) oz_arrive(&full[st]);
+    }
+  } else if (warp == 4) {
+    if (lane == 0) {
+      // ---------------- products
+      for (int s = 0; s < nsl && !*abort_flag; ++s) {
+        const int st = s & 1;
+        const int ks = c0 * (OZ_KC / OZ_BK) + s;
+        const int chl = ks / (OZ_KC / OZ_BK) - c0, a = chl % TL::NSETS;
+        const bool first_sl = s == 0 || (ks % (OZ_KC / OZ_BK)) == 0;
+        const bool last_sl = s == nsl - 1 || ((ks + 1) % (OZ_KC / OZ_BK)) == 0;
+        if (first_sl && chl >= TL::NSETS && !oz_wait(&acce[a], (chl / TL::NSETS - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (!oz_wait(&full[st], (s >> 1) & 1)) { *abort_flag = 1; break; }
+        oz_fence_after();
+        const unsigned char* stg = sm + st * TL::STAGE;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+          for (int pa = 0; pa < OZ_S; ++pa) {
+#pragma unroll
+            for (int pb = 0; pb < OZ_S - pa; ++pb) {
+              const int t = pa + pb, g = t < OZ_NACC - 1 ? t : OZ_NACC - 1;
+              const bool first = first_sl && kk == 0 && pa == 0 && (g < OZ_NACC - 1 || t == OZ_NACC - 1);
+              oz_mma(tmem + (uint32_t)(TL::SETW * a + g * BN), oz_desc(oz_smem(stg + pa * TL::PLANE_A) + 32 * kk),
+                     oz_desc(oz_smem(stg + OZ_S * TL::PLANE_A + pb * TL::PLANE_B) + 32 * kk), idesc,
+                     first ? 0u : 1u);
+            }
+          }
+        }
+        oz_commit(&empty[st]);
+        if (last_sl) oz_commit(&accf[a]);
+        committed = s + 1;
+      }
+    }
+  } else {
+    // ---------------- epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of this CTA)
+    const int row = 32 * warp + lane;
+    const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+    for (int j = 0; j < c1 - c0; ++j) {
+      if (__any_sync(0xffffffffu, *abort_flag)) break;
+      const int a = j % TL::NSETS;
+      const bool ok = oz_wait(&accf[a], (j / TL::NSETS) & 1);
+      if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; break; }
+      oz_fence_after();
+      const int ch = c0 + j;
+      const int ea = row < p.M ? __ldg(p.exA + ((size_t)bA * p.nch + ch) * p.M + row) : -2000;
+      const int* eB = p.exB + ((size_t)bB * p.nch + ch) * p.N + n0;
+#pragma unroll 1
+      for (int h = 0; h < BN / 8; ++h) {
+        uint32_t ra[8], rb[8], rc[8], rd[8], rt[8];
+        const uint32_t base = tmem + lanes + (uint32_t)(TL::SETW * a + 8 * h);
+        oz_ld8(base, ra);
+        oz_ld8(base + (uint32_t)BN, rb);
+        oz_ld8(base + (uint32_t)(2 * BN), rc);
+        oz_ld8(base + (uint32_t)(3 * BN), rd);
+        oz_ld8(base + (uint32_t)(4 * BN), rt);
+        oz_ld_wait();
+        if (row < p.M) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int col = 8 * h + q;
+            if (col < nv) sums[col * AR + row] += oz_combine(ra[q], rb[q], rc[q], rd[q], rt[q], ea, __ldg(eB + col));
+          }
+        }
+      }
+      oz_fence_before();
+      __syncwarp();
+      if (lane == 0) oz_arrive(&acce[a]);
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    if (tid == 0) atomicExch(&g_oz_status, HODLR_ETIMEOUT);
+    // the MMAs already issued complete before the TMEM is freed (the producers issue no
+    // asynchronous copies)
+    if (warp == 4 && lane == 0 && committed > 0) oz_wait(&empty[(committed - 1) & 1], ((committed - 1) >> 1) & 1);
+  } else {
+    for (int i = tid; i < AR * BN; i += AT_THREADS) {
+      const int col = i / AR, row = i % AR;
+      if (row >= p.M || col >= nv) continue;
+      const double v = sums[i];
+      if (p.nrange == 1) {
+        double* c = p.C + (size_t)b * p.sC + (size_t)(n0 + col) * p.ldc + row;
+        double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
+        if (p.beta != 0.0) out = p.beta == 1.0 ? *c + out : fma(p.beta, *c, out);
+        *c = out;
+      } else {
+        p.part[((size_t)b * p.nrange + range) * ((size_t)p.M * p.N) + (size_t)(n0 + col) * p.M + row] = v;
+      }
+    }
+  }
+  oz_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    oz_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- fused short-K products
+// C_b = alpha A_b op(B_b) + beta C_b with A column-major (M x K, consecutive rows adjacent), K at
+// most 64 and M large: the peeling updates of Alg. 1 (M block rows, K the rank, N the probe
+// columns), bound by the FP64 traffic of C.  One CTA per SM loops over 128-row tiles of A:
+//   warps 10..15 (producers): read the tile's rows in FP64 (lanes on consecutive rows), cut
+//       them into digits with the row exponents and store all K slices of the seven planes into
+//       the A buffer (112 KB), once the MMAs of the previous tile are done with it;
+//   warp 8 (one thread): TMA loads of the B planes (sliced beforehand; small and L2-resident)
+//       for each 48-column subtile and slice into a ring of three 21 KB stages;
+//   warp 9 (one thread): the 56 MMAs of each (subtile, slice) into one of two TMEM sets;
+//   warps 0..7: the epilogue of each subtile (warps w and w + 4 share TMEM lane quarter w,
+//       24 columns each), with the C loads of the next eight columns issued ahead of their use.
+constexpr int AB_BN = 48, AB_NST = 3, AB_KMAX = 64, AB_NPROD = 6;
+constexpr int AB_THREADS = 32 * (10 + AB_NPROD);
+constexpr int AB_PLANE_B = AB_BN * 64;                                   // 3 KB
+constexpr int AB_APLANE = (AB_KMAX / OZ_BK) * OZ_PLANE_A;                // 16 KB: one plane, all slices
+constexpr int AB_ABUF = OZ_S * AB_APLANE;                                // 112 KB
+constexpr int AB_STAGE = OZ_S * AB_PLANE_B;                              // 21 KB
+constexpr int AB_SMEM = AB_ABUF + AB_NST * AB_STAGE + 1024 + 256;
+
+struct AbParams {
+  const double* A;        // A_b = A + bA sA, element (i, k) at A_b[i + k lda]
+  long long lda, sA;
+  int M, N, K, Kp, nbA, nbB, bmap;
+  int ntm, ntn, ntiles;   // 128-row tiles per product, 48-column subtiles, tiles in all
+  const int *exA, *exB;   // [nbA][M], [nbB][N]
+  double alpha, beta;
+  double* C;
+  long long ldc, sC;
+};
+
+__global__ void __launch_bounds__(AB_THREADS, 1)
+    oz_ab_kernel(const __grid_constant__ CUtensorMap mapB, const AbParams p) {
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* abuf = sm;
+  unsigned char* bst = sm + AB_ABUF;
+  uint64_t* full = (uint64_t*)(bst + AB_NST * AB_STAGE);
+  uint64_t* empty = full + AB_NST;
+  uint64_t* accf = empty + AB_NST;
+  uint64_t* acce = accf + 2;
+  uint64_t* afull = acce + 2;
+  uint64_t* afree = afull + 1;
+  volatile int* abort_flag = (volatile int*)(afree + 1);
+  uint32_t* tslot = (uint32_t*)(afree + 1) + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nk = p.Kp / OZ_BK;   // 1 or 2 slices
+  if (tid == 0) {
+    for (int s = 0; s < AB_NST; ++s) {
+      oz_mbar_init(&full[s], 1);
+      oz_mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      oz_mbar_init(&accf[a], 1);
+      oz_mbar_init(&acce[a], 8);
+    }
+    oz_mbar_init(afull, AB_NPROD);
+    oz_mbar_init(afree, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(oz_smem(tslot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  oz_fence_before();
+  __syncthreads();
+  oz_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(AB_BN >> 3) << 17) |
+                         ((uint32_t)(OZ_BM >> 4) << 24);
+  auto bidx = [&](int b) {
+    return p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
+  };
+  int issued = 0, committed = 0;   // TMA / MMA progress (slices), for the drain after an abort
+  if (warp >= 10) {
+    // ---------------- A producers
+    const int ptid = tid - 10 * 32;
+    int j = 0;
+    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++j) {
+      if (__any_sync(0xffffffffu, *abort_flag)) break;
+      if (j > 0) {
+        const bool ok = oz_wait(afree, (j - 1) & 1);
+        if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; break; }
+      }
+      const int b = t / p.ntm, m0 = (t % p.ntm) * OZ_BM;
+      const int bA = p.nbA == 1 ? 0 : b;
+      const double* Ab = p.A + (size_t)bA * p.sA;
+      const int tasks = OZ_BM * (p.Kp / 8);
+      for (int u = ptid; u < tasks; u += 32 * AB_NPROD) {
+        const int r = u % OZ_BM, qq = u / OZ_BM;   // lanes on consecutive rows
+        const int row = m0 + r, k0 = 8 * qq;
+        const bool live = row < p.M;
+        const int e = live ? __ldg(p.exA + (size_t)bA * p.M + row) : -2000;
+        double x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = live && k0 + i < p.K ? __ldg(Ab + row + (size_t)(k0 + i) * p.lda) : 0.0;
+        oz_put8(x, e, abuf + (qq >> 2) * OZ_PLANE_A, r, qq & 3, AB_APLANE);
+      }
+      oz_fence_async_smem();
+      __syncwarp();
+      if (lane == 0) oz_arrive(afull);
+    }
+  } else if (warp == 8) {
+    if (lane == 0) {
+      // ---------------- B loads
+      int it = 0;
+      for (int t = blockIdx.x; t < p.ntiles && !*abort_flag; t += gridDim.x) {
+        const int bB = bidx(t / p.ntm);
+        for (int n = 0; n < p.ntn && !*abort_flag; ++n)
+          for (int s = 0; s < nk; ++s, ++it) {
+            const int st = it % AB_NST, u = it / AB_NST;
+            if (u > 0 && !oz_wait(&empty[st], (u - 1) & 1)) { *abort_flag = 1; break; }
+            oz_expect_tx(&full[st], AB_STAGE);
+#pragma unroll
+            for (int q = 0; q < OZ_S; ++q)
+              oz_tma3(bst + st * AB_STAGE + q * AB_PLANE_B, &mapB, s * OZ_BK, n * AB_BN, q * p.nbB + bB, &full[st]);
+            issued = it + 1;
+          }
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // ---------------- products
+      int it = 0, jt = 0, j = 0;
+      for (int t = blockIdx.x; t < p.ntiles && !*abort_flag; t += gridDim.x, ++j) {
+        if (!oz_wait(afull, j & 1)) { *abort_flag = 1; break; }
+        oz_fence_after();
+        bool ok = true;
+        for (int n = 0; n < p.ntn && ok; ++n, ++jt) {
+          const int a = jt & 1;
+          if (jt >= 2 && !oz_wait(&acce[a], ((jt >> 1) - 1) & 1)) { ok = false; break; }
+          oz_fence_after();
+          for (int s = 0; s < nk; ++s, ++it) {
+            const int st = it % AB_NST;
+            if (!oz_wait(&full[st], (it / AB_NST) & 1)) { ok = false; break; }
+            oz_fence_after();
+            const unsigned char* bs = bst + st * AB_STAGE;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+              for (int pa = 0; pa < OZ_S; ++pa) {
+#pragma unroll
+                for (int pb = 0; pb < OZ_S - pa; ++pb) {
+                  const int tt = pa + pb, g = tt < OZ_NACC - 1 ? tt : OZ_NACC - 1;
+                  const bool first = s == 0 && kk == 0 && pa == 0 && (g < OZ_NACC - 1 || tt == OZ_NACC - 1);
+                  oz_mma(tmem + (uint32_t)(256 * a + g * AB_BN),
+                         oz_desc(oz_smem(abuf + pa * AB_APLANE + s * OZ_PLANE_A) + 32 * kk),
+                         oz_desc(oz_smem(bs + pb * AB_PLANE_B) + 32 * kk), idesc, first ? 0u : 1u);
+                }
+              }
+            }
+            oz_commit(&empty[st]);
+            committed = it + 1;
+          }
+          if (ok) oz_commit(&accf[a]);
+        }
+        if (!ok) { *abort_flag = 1; break; }
+        oz_commit(afree);   // the A buffer is free once this tile's products have completed
+      }
+    }
+  } else {
+    // ---------------- epilogue
+    const int wq = warp & 3, wh = warp >> 2;
+    const uint32_t lanes = (uint32_t)(32 * wq) << 16;
+    int jt = 0;
+    for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+      if (__any_sync(0xffffffffu, *abort_flag)) break;
+      const int b = t / p.ntm, m0 = (t % p.ntm) * OZ_BM;
+      const int bA = p.nbA == 1 ? 0 : b, bB = bidx(b);
+      const int row = m0 + 32 * wq + lane;
+      const bool live = row < p.M;
+      const int ea = live ? __ldg(p.exA + (size_t)bA * p.M + row) : -2000;
+      double* crow = p.C + (size_t)b * p.sC + row;
+      bool stop = false;
+      for (int n = 0; n < p.ntn; ++n, ++jt) {
+        const int a = jt & 1;
+        const int c0 = n * AB_BN + (AB_BN / 2) * wh;
+        double cv[8], cn[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          cv[q] = p.beta != 0.0 && live && c0 + q < p.N ? crow[(size_t)(c0 + q) * p.ldc] : 0.0;
+        const bool ok = oz_wait(&accf[a], (jt >> 1) & 1);
+        if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; stop = true; break; }
+        oz_fence_after();
+#pragma unroll
+        for (int h = 0; h < AB_BN / 16; ++h) {
+          const int cc = c0 + 8 * h;
+          if (h + 1 < AB_BN / 16) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              cn[q] = p.beta != 0.0 && live && cc + 8 + q < p.N ? crow[(size_t)(cc + 8 + q) * p.ldc] : 0.0;
+          }
+          uint32_t ra[8], rb[8], rc[8], rd[8], rt[8];
+          const uint32_t base = tmem + lanes + (uint32_t)(256 * a + (AB_BN / 2) * wh + 8 * h);
+          oz_ld8(base, ra);
+          oz_ld8(base + (uint32_t)AB_BN, rb);
+          oz_ld8(base + (uint32_t)(2 * AB_BN), rc);
+          oz_ld8(base + (uint32_t)(3 * AB_BN), rd);
+          oz_ld8(base + (uint32_t)(4 * AB_BN), rt);
+          oz_ld_wait();
+          if (h + 1 == AB_BN / 16) {
+            // the accumulator set is free for the subtile after next
+            oz_fence_before();
+            __syncwarp();
+            if (lane == 0) oz_arrive(&acce[a]);
+          }
+          if (live) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int col = cc + q;
+              if (col >= p.N) continue;
+              const double v = oz_combine(ra[q], rb[q], rc[q], rd[q], rt[q], ea, __ldg(p.exB + (size_t)bB * p.N + col));
+              double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
+              if (p.beta != 0.0) out = p.beta == 1.0 ? cv[q] + out : fma(p.beta, cv[q], out);
+              crow[(size_t)col * p.ldc] = out;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) cv[q] = cn[q];
+        }
+      }
+      if (stop) break;
+    }
+  }
+  __syncthreads();
+  if (*abort_flag) {
+    if (tid == 0) atomicExch(&g_oz_status, HODLR_ETIMEOUT);
+    if (warp == 8 && lane == 0)
+      for (int it = issued - 1; it >= 0 && it >= issued - AB_NST; --it) oz_wait(&full[it % AB_NST], (it / AB_NST) & 1);
+    if (warp == 9 && lane == 0 && committed > 0)
+      oz_wait(&empty[(committed - 1) % AB_NST], ((committed - 1) / AB_NST) & 1);
+  }
+  oz_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    oz_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ordered reduction of the split-K partials (FP64), then alpha / beta
 __global__ void oz_reduce_kernel(int M, int N, int nsplit, const double* part, double alpha, double beta, double* C,
                                  long long ldc, long long sC) {
   const int b = blockIdx.y;
@@ -772,6 +1323,132 @@ static size_t oz_bytes(int nbA, int M, int nbB, int N, int Kp) {
          align256((size_t)nbA * M * 4) + align256((size_t)nbB * N * 4);
 }
 
+static int oz_num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    HODLR_CUDA(cudaGetDevice(&dev));
+    HODLR_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
+struct OzProf {   // CUDA events around a product launch (the context's profile)
+  bool on;
+  explicit OzProf(cudaStream_t st) : on(g_prof.on && g_prof.n < g_prof.cap) {
+    if (on) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
+  }
+  void done(const GemmArgs& g, int nc, int nb, int variant, cudaStream_t st) {
+    if (!on) return;
+    cudaEventRecord(g_prof.ev[2 * g_prof.n + 1], st);
+    if (g_prof.shape) {
+      int* sh = g_prof.shape + 7 * g_prof.n;
+      sh[0] = g.M; sh[1] = nc; sh[2] = g.K; sh[3] = nb; sh[4] = g.tA; sh[5] = g.tB; sh[6] = variant;
+    }
+    ++g_prof.n;
+    g_prof.flops += 2.0 * (double)g.M * nc * g.K * nb;
+    prof_add_bytes(variant, ((double)g.M * g.K + (double)g.K * nc + (double)g.M * nc * (g.beta != 0.0 ? 2 : 1)) * 8.0 * nb);
+  }
+};
+
+// The fused products (digits made in shared memory by the product kernel): long-K A^T B with
+// M <= 128, and short-K A B with column-major A and K <= 64.  False when the shape is not one of
+// them or its exponents (and the B planes of a short-K product) do not fit the workspace.
+static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st) {
+  const Scratch w = g_oz_cfg.work;
+  const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  const int nb = g.batch;
+  const bool sharedA = g.sA == 0, sharedB = g.sB == 0;
+  const int nbA = sharedA ? 1 : nb;
+  const int nbB = sharedB ? 1 : (g.bmap == BMAP_SHR1 ? (nb + 1) / 2 : nb);
+  const int bmap = sharedB ? BMAP_ID : g.bmap;
+  if (g.tA && !g.tB && g.M <= OZ_BM && Kp >= 2 * OZ_KC && nb <= 65535) {
+    const int nch = cdiv(Kp, OZ_KC);
+    const bool small = g.M <= 64;
+    const int bn = small ? 80 : 48;
+    const int nparts = cdiv(g.N, bn);
+    const size_t ea_bytes = align256((size_t)nbA * nch * g.M * 4);
+    if (ea_bytes + align256((size_t)nbB * nch * g.N * 4) > w.bytes) return false;
+    int* eA = (int*)w.ptr;
+    int* eB = (int*)((char*)w.ptr + ea_bytes);
+    // ranges of chunks per CTA: about one CTA per SM over all products and column parts
+    const long long tasks = (long long)nb * nparts * nch;
+    int cpr = (int)std::max<long long>(1, (tasks + oz_num_sms() - 1) / oz_num_sms());
+    int nrange = cdiv(nch, cpr);
+    while (nrange > 1 && (size_t)nb * nrange * g.M * g.N * 8 > split.bytes) {
+      cpr *= 2;
+      nrange = cdiv(nch, cpr);
+    }
+    if (nrange > 65535 || nparts > 65535) return false;
+    OzView va{(const double*)g.A, g.sA, g.lda, 1, nbA, g.M, g.K};
+    OzView vb{(const double*)g.B, g.sB, g.ldb, 1, nbB, g.N, g.K};
+    oz_exp_chunks_kernel<<<dim3(cdiv(g.M, 8), nch, nbA), 256, 0, st>>>(va, OZ_KC, nch, eA);
+    check_launch("oz_exp_chunks");
+    oz_exp_chunks_kernel<<<dim3(cdiv(g.N, 8), nch, nbB), 256, 0, st>>>(vb, OZ_KC, nch, eB);
+    check_launch("oz_exp_chunks");
+    AtParams p{};
+    p.A = (const double*)g.A; p.B = (const double*)g.B;
+    p.lda = g.lda; p.sA = g.sA; p.ldb = g.ldb; p.sB = g.sB;
+    p.M = g.M; p.N = g.N; p.K = g.K; p.nbA = nbA; p.nbB = nbB; p.bmap = bmap;
+    p.nch = nch; p.cpr = cpr; p.nrange = nrange;
+    p.exA = eA; p.exB = eB; p.alpha = g.alpha; p.beta = g.beta;
+    p.C = (double*)g.C; p.ldc = g.ldc; p.sC = g.sC; p.part = (double*)split.ptr;
+    const dim3 grid(nparts, nrange, nb);
+    OzProf prof(st);
+    if (small) {
+      using TL = AtTile<64, 80>;
+      HODLR_CUDA(cudaFuncSetAttribute(oz_atb_kernel<64, 80>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM));
+      oz_atb_kernel<64, 80><<<grid, AT_THREADS, TL::SMEM, st>>>(p);
+    } else {
+      using TL = AtTile<128, 48>;
+      HODLR_CUDA(cudaFuncSetAttribute(oz_atb_kernel<128, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM));
+      oz_atb_kernel<128, 48><<<grid, AT_THREADS, TL::SMEM, st>>>(p);
+    }
+    check_launch("oz_atb_kernel");
+    prof.done(g, g.N, nb, 6, st);
+    if (nrange > 1) {
+      oz_reduce_kernel<<<dim3(cdiv((long long)g.M * g.N, 256), nb), 256, 0, st>>>(g.M, g.N, nrange, p.part, g.alpha,
+                                                                                g.beta, p.C, g.ldc, g.sC);
+      check_launch("oz_reduce");
+    }
+    return true;
+  }
+  if (!g.tA && Kp <= AB_KMAX && g.M >= OZ_BM && (long long)g.M * nb >= 4096) {
+    const size_t pb_bytes = align256((size_t)OZ_S * nbB * g.N * Kp * 2);
+    const size_t eb_bytes = align256((size_t)nbB * g.N * 4);
+    if (pb_bytes + eb_bytes + align256((size_t)nbA * g.M * 4) > w.bytes) return false;
+    __nv_bfloat16* pB = (__nv_bfloat16*)w.ptr;
+    int* eB = (int*)((char*)w.ptr + pb_bytes);
+    int* eA = (int*)((char*)w.ptr + pb_bytes + eb_bytes);
+    OzView vb;
+    vb.base = (const double*)g.B; vb.sb = g.sB; vb.nb = nbB; vb.R = g.N; vb.K = g.K;
+    if (g.tB) { vb.sr = 1; vb.sk = g.ldb; } else { vb.sr = g.ldb; vb.sk = 1; }
+    oz_slice(vb, Kp, eB, pB, st);
+    CUtensorMap mb;
+    if (!oz_map(&mb, pB, Kp, g.N, OZ_S * nbB, AB_BN)) throw Error(HODLR_ECUDA, "oz_gemm: tensor map");
+    OzView va{(const double*)g.A, g.sA, 1, g.lda, nbA, g.M, g.K};
+    oz_exp_chunks_kernel<<<dim3(cdiv(g.M, 256), 1, nbA), 256, 0, st>>>(va, Kp, 1, eA);
+    check_launch("oz_exp_chunks");
+    AbParams p{};
+    p.A = (const double*)g.A; p.lda = g.lda; p.sA = g.sA;
+    p.M = g.M; p.N = g.N; p.K = g.K; p.Kp = Kp; p.nbA = nbA; p.nbB = nbB; p.bmap = bmap;
+    p.ntm = cdiv(g.M, OZ_BM); p.ntn = cdiv(g.N, AB_BN);
+    const long long ntiles = (long long)nb * p.ntm;
+    if (ntiles > 0x7fffffffLL) return false;
+    p.ntiles = (int)ntiles;
+    p.exA = eA; p.exB = eB; p.alpha = g.alpha; p.beta = g.beta;
+    p.C = (double*)g.C; p.ldc = g.ldc; p.sC = g.sC;
+    const int ctas = (int)std::min<long long>(ntiles, oz_num_sms());
+    OzProf prof(st);
+    HODLR_CUDA(cudaFuncSetAttribute(oz_ab_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AB_SMEM));
+    oz_ab_kernel<<<ctas, AB_THREADS, AB_SMEM, st>>>(mb, p);
+    check_launch("oz_ab_kernel");
+    prof.done(g, g.N, nb, 7, st);
+    return true;
+  }
+  return false;
+}
+
 bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st) {
   if (!oz_eligible(g)) return false;
   return oz_gemm_any(g, split, st);
@@ -779,6 +1456,7 @@ bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st) {
 
 bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
   if (!g_oz_cfg.work.ptr || g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
+  if (oz_fused(g, split, st)) return true;
   const Scratch w = g_oz_cfg.work;
   const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
   const size_t nsp = (size_t)cdiv(Kp, OZ_KC);   // one 512-long chunk of K per CTA
@@ -896,7 +1574,7 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
         }
         ++g_prof.n;
         g_prof.flops += 2.0 * (double)g.M * nc * g.K * nb;
-        g_prof.bytes += ((double)g.M * g.K + (double)g.K * nc + (double)g.M * nc * (g.beta != 0.0 ? 2 : 1)) * 8.0 * nb;
+        prof_add_bytes(5, ((double)g.M * g.K + (double)g.K * nc + (double)g.M * nc * (g.beta != 0.0 ? 2 : 1)) * 8.0 * nb);
       }
       if (nsplit > 1) {
         dim3 rg(cdiv((long long)g.M * nc, 256), nb);

@@ -417,7 +417,7 @@ void tc_launch(const CUtensorMap& ma, const CUtensorMap& ml, const CUtensorMap& 
     }
     ++g_prof.n;
     g_prof.flops += 2.0 * (double)p.M * p.N * p.K * batch;
-    g_prof.bytes += ((double)p.M * p.K + (double)p.K * p.N + (double)p.M * p.N) * 4.0 * batch;
+    prof_add_bytes(4, ((double)p.M * p.K + (double)p.K * p.N + (double)p.M * p.N) * 4.0 * batch);
   }
 }
 }  // namespace

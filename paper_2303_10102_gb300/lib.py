@@ -282,12 +282,13 @@ class Hodlr:
         self._check(self.lib.hodlr_profile(self.h, int(bool(enable))))
 
     FAMILIES = ("gemm_kernel", "sgemm_large_kernel", "gemm_df_kernel", "gemv_kernel", "tf32x3_gemm_kernel",
-                "oz_mma_kernel")
+                "oz_mma_kernel", "oz_atb_kernel", "oz_ab_kernel")
 
     def profile_read(self):
-        out = np.zeros(22)
+        out = np.zeros(4 + 4 * len(self.FAMILIES))
         self._check(self.lib.hodlr_profile_read(self.h, _dp(out)))
-        fam = {name: {"ms": float(out[4 + 3 * v]), "flops": float(out[5 + 3 * v]), "launches": int(out[6 + 3 * v])}
+        fam = {name: {"ms": float(out[4 + 4 * v]), "flops": float(out[5 + 4 * v]), "launches": int(out[6 + 4 * v]),
+                      "bytes": float(out[7 + 4 * v])}
                for v, name in enumerate(self.FAMILIES)}
         return {"ms": float(out[0]), "launches": int(out[1]), "flops": float(out[2]), "bytes": float(out[3]),
                 "families": fam}

@@ -246,6 +246,19 @@ def test_error_paths():
     assert np.isfinite(h.nll(w.theta, y))
 
 
+@pytest.mark.parametrize("dim,G,nvar,leaf", [(2, 3, 1, 2), (2, 100, 1, 64), (2, 129, 2, 32), (2, 1000, 1, 256),
+                                               (1, 40961, 1, 64), (1, 4097, 2, 128)])
+def test_device_tree_order_uneven_grids(dim, G, nvar, leaf):
+    """a1 on the device: the tree_order kernel's maps (read back by hodlr_perm) equal the oracle's
+    sorted Morton order and halving tree bit for bit on grids whose side is not a power of two
+    and trees whose leaves differ in size."""
+    from paper_2303_10102_gb300 import Hodlr
+    t = Tree(dim, G, nvar, leaf)
+    h = Hodlr(dim, G, nvar, 1.5, "fp64", leaf, 2, 0, 0.0, 1, device=DEV)
+    assert h.N == t.N and h.tau == t.tau
+    assert np.array_equal(h.perm(), t.perm)
+
+
 @pytest.mark.parametrize("name", ["C1", "C2", "C4"])
 def test_full_size_tree_order_bit_exact(name):
     w = synth.workload(name)
@@ -255,7 +268,7 @@ def test_full_size_tree_order_bit_exact(name):
     lib = plib.load()
     m = plib.Model(w.dim, (ctypes.c_int * 2)(w.G, w.G if w.dim == 2 else 1), w.nvar, w.nu, 1)
     o = plib.Opts(w.leaf, w.cap, w.c - w.cap, w.tol, 1, 0.0)
-    # a context needs its workspace; the tree order itself is host data
+    # the context's tree order comes from the device kernel (closed-form Morton rank per point)
     nbytes = lib.hodlr_workspace_size(ctypes.byref(m), ctypes.byref(o))
     assert nbytes > 0
     h = ctx(w, "fp32")

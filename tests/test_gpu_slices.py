@@ -148,3 +148,95 @@ def test_long_k_split_into_ranges_and_short_k_tiles():
         ref = A @ B
         assert np.all(np.abs(got - ref) <= 1.5 * _bound(A, B)), (M, N, K)
         assert np.linalg.norm(got - ref) <= 5e-13 * np.linalg.norm(ref), (M, N, K)
+
+
+# ---------------------------------------------------------------- fused products
+# Short-K A B with column-major A (K <= 64, M x batch >= 4096) and long-K A^T B with M <= 128
+# (K >= 1024) make their digit planes in shared memory (oz_ab_kernel / oz_atb_kernel) instead of
+# reading sliced planes; the long-K product scales each 512-long chunk of K by its own exponents.
+
+@pytest.mark.parametrize("M,N,K", [(5000, 130, 37), (4096 + 17, 136, 64), (300, 50, 8)])
+def test_fused_short_k_integer_operands_are_exact(M, N, K):
+    rng = np.random.default_rng(M + K)
+    nb = 1 if M * 1 >= 4096 else 16   # 300 x 16 rows: the batch reaches the fused path
+    As = [rng.integers(-1000, 1001, size=(M, K)).astype(np.float64) for _ in range(nb)]
+    Bs = [rng.integers(-1000, 1001, size=(K, N)).astype(np.float64) for _ in range(nb)]
+    A = torch.cat([colmajor(a) for a in As])
+    B = torch.cat([colmajor(b) for b in Bs])
+    C = torch.zeros(nb * M * N, dtype=torch.float64, device=DEV)
+    assert slices(A, B, M, N, K, nb, M, M * K, 0, K, K * N, 0, 0, 1.0, 0.0, C, M, M * N) == 0
+    got = C.cpu().numpy().reshape(nb, N, M).transpose(0, 2, 1)
+    for b in range(nb):
+        ref = (As[b].astype(np.int64) @ Bs[b].astype(np.int64)).astype(np.float64)
+        assert np.array_equal(got[b], ref), b
+
+
+def test_fused_short_k_scaled_operands_layouts_and_batches():
+    rng = np.random.default_rng(21)
+    # one product: rows of A and columns of B over six decades, B given transposed, alpha / beta
+    M, N, K = 3 * 4096 + 5, 136, 61
+    A = rng.standard_normal((M, K)) * 10.0 ** rng.uniform(-3, 3, size=(M, 1))
+    B = rng.standard_normal((K, N)) * 10.0 ** rng.uniform(-3, 3, size=(1, N))
+    C0 = rng.standard_normal((M, N))
+    C = colmajor(C0)
+    assert slices(colmajor(A), colmajor(B.T), M, N, K, 1, M, 0, 0, N, 0, 1, 0, -1.5, 0.5, C, M, 0) == 0
+    got = C.cpu().numpy().reshape(N, M).T
+    ref = -1.5 * (A @ B) + 0.5 * C0
+    assert np.all(np.abs(got - ref) <= 1.5 * 1.5 * _bound(A, B) + 1e-15 * np.abs(ref))
+    assert np.linalg.norm(got - ref) <= 5e-13 * np.linalg.norm(ref)
+    # batches: paired B operands (b^1) and one shared A, with ragged M and a C leading dimension
+    # larger than M
+    M, N, K, nb, ldc = 1030, 70, 33, 6, 1040
+    As = [_scaled(rng, M, K) for _ in range(nb)]
+    Bs = [_scaled(rng, K, N) for _ in range(nb)]
+    A = torch.cat([colmajor(a) for a in As])
+    B = torch.cat([colmajor(b) for b in Bs])
+    for bmap, sA, pick in [(1, M * K, lambda b: (As[b], Bs[b ^ 1])), (2, 0, lambda b: (As[0], Bs[b >> 1]))]:
+        C = torch.zeros(nb * ldc * N, dtype=torch.float64, device=DEV)
+        assert slices(A, B, M, N, K, nb, M, sA, 0, K, K * N, 0, bmap, 1.0, 0.0, C, ldc, ldc * N) == 0
+        got = C.cpu().numpy().reshape(nb, N, ldc).transpose(0, 2, 1)
+        for b in range(nb):
+            a, bb = pick(b)
+            assert np.all(np.abs(got[b, :M] - a @ bb) <= 1.5 * _bound(a, bb)), (bmap, b)
+            assert np.all(got[b, M:] == 0.0)
+
+
+@pytest.mark.parametrize("M,N,K", [(64, 136, 40000), (100, 130, 5000), (1, 7, 1024)])
+def test_fused_long_k_integer_operands_are_exact(M, N, K):
+    """Integer operands whose products and partial sums are exact in FP64: each 512-long chunk
+    with its own exponents, the chunks of a CTA summed in FP64, the CTAs' partials reduced."""
+    rng = np.random.default_rng(M * 7 + N)
+    A = rng.integers(-1000, 1001, size=(M, K)).astype(np.float64)
+    B = rng.integers(-1000, 1001, size=(K, N)).astype(np.float64)
+    A[:, 1000:1700] *= 1024.0      # chunks of very different magnitude
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    C = torch.zeros(M * N, dtype=torch.float64, device=DEV)
+    assert slices(colmajor(A.T), colmajor(B), M, N, K, 1, K, 0, 1, K, 0, 0, 0, 1.0, 0.0, C, M, 0) == 0
+    got = C.cpu().numpy().reshape(N, M).T
+    assert np.array_equal(got, ref)
+
+
+def test_fused_long_k_scaled_operands_ragged_and_batched():
+    rng = np.random.default_rng(22)
+    for M, N, K in [(64, 136, 33333), (128, 48, 2049), (37, 200, 100001)]:
+        A = rng.standard_normal((M, K)) * 10.0 ** rng.uniform(-3, 3, size=(M, 1))
+        B = rng.standard_normal((K, N)) * 10.0 ** rng.uniform(-3, 3, size=(1, N))
+        C0 = rng.standard_normal((M, N))
+        C = colmajor(C0)
+        assert slices(colmajor(A.T), colmajor(B), M, N, K, 1, K, 0, 1, K, 0, 0, 0, 2.0, -1.0, C, M, 0) == 0
+        got = C.cpu().numpy().reshape(N, M).T
+        ref = 2.0 * (A @ B) - C0
+        assert np.all(np.abs(got - ref) <= 2 * 1.5 * _bound(A, B) + 1e-15 * np.abs(ref)), (M, N, K)
+        assert np.linalg.norm(got - ref) <= 5e-13 * np.linalg.norm(ref), (M, N, K)
+    # batch of 5 with one shared B and with B_(b>>1)
+    M, N, K, nb = 45, 136, 4096, 5
+    As = [_scaled(rng, M, K) for _ in range(nb)]
+    Bs = [_scaled(rng, K, N) for _ in range(nb)]
+    A = torch.cat([colmajor(a.T) for a in As])
+    B = torch.cat([colmajor(b) for b in Bs])
+    for bmap, sB, pick in [(0, 0, lambda b: Bs[0]), (2, K * N, lambda b: Bs[b >> 1])]:
+        C = torch.zeros(nb * M * N, dtype=torch.float64, device=DEV)
+        assert slices(A, B, M, N, K, nb, K, M * K, 1, K, sB, 0, bmap, 1.0, 0.0, C, M, M * N) == 0
+        got = C.cpu().numpy().reshape(nb, N, M).transpose(0, 2, 1)
+        for b in range(nb):
+            assert np.all(np.abs(got[b] - As[b] @ pick(b)) <= 1.5 * _bound(As[b], pick(b))), (bmap, b)

@@ -75,8 +75,9 @@ def test_workspace_plan_rejects_bad_options(so_path):
 @pytest.mark.parametrize("name", ["C0", "C1", "C2", "C2L", "C4"])
 def test_tree_order_bit_exact_at_full_size(so_path, name):
     """a1 (KD / Morton ordering and the cluster tree, Sec. 5.2 and Sec. 3.2.2): the library's host
-    plan (hodlr_plan, no device work) equals the oracle's tree bit for bit at the workloads' full
-    sizes, up to N = 2^21."""
+    plan (hodlr_plan, no device work; the closed-form Morton rank and halving walk that the
+    device kernel runs) equals the oracle's tree (a sort of the Morton keys) bit for bit at the
+    workloads' full sizes, up to N = 2^21."""
     from oracle.tree import Tree
     import numpy as np
     w = synth.workload(name)
@@ -94,10 +95,13 @@ def test_tree_order_bit_exact_at_full_size(so_path, name):
 
 
 @pytest.mark.parametrize("dim,G,nvar,leaf", [(1, 99, 1, 32), (1, 1000, 1, 64), (1, 40961, 1, 64),
-                                               (1, 4097, 2, 128), (2, 23, 1, 64), (2, 45, 2, 128)])
+                                               (1, 4097, 2, 128), (2, 23, 1, 64), (2, 45, 2, 128),
+                                               (2, 3, 1, 2), (2, 100, 1, 64), (2, 129, 2, 32), (2, 1000, 1, 256)])
 def test_uneven_trees_match_the_oracle_bit_exactly(so_path, dim, G, nvar, leaf):
     """Median splits of a size that is not leaf x 2^tau (Sec. 3.2.2 index sets) give leaves whose
-    sizes differ by one: the library's plan equals the oracle's tree order bit for bit."""
+    sizes differ by one, and 2-D grids of a side that is not a power of two give Morton ranks
+    that are not the keys themselves: the library's plan equals the oracle's tree order bit for
+    bit."""
     import numpy as np
     from oracle.tree import Tree
     lib = plib.load()
