@@ -258,6 +258,25 @@ int hodlr_dgemm_slices(int M, int N, int K, int batch, const double* A, long lon
                        const double* B, long long ldb, long long sB, int tB, int bmap, double alpha, double beta,
                        double* C, long long ldc, long long sC, void* work, size_t work_bytes, void* cuda_stream);
 
+/* Tile autotuner (the project's own, for the batched workloads' kernel choices).  With
+ * enable != 0 the context's later builds and evaluations (HODLR_MIXED_BF16 contexts; not
+ * inside a captured graph) time, at the first occurrence of each digit-slice product shape,
+ * every candidate plan: the product from slice planes in the workspace, and where the shape
+ * allows, the fused kernels with either tile (64 x 80 or 128 x 48 for long-K A^T B) and one or
+ * four times the default chunks of K per CTA.  Each candidate runs once to warm up and twice
+ * timed (CUDA events on the context's stream) into a scratch C carved from the slice
+ * workspace; the fastest plan is remembered for the process (all contexts and threads) and
+ * the product then runs with it, so results are those of the chosen kernels.  Shapes whose
+ * scratch C would exceed half the slice workspace keep the default plan.  enable = 0 stops
+ * tuning; remembered plans stay in use.  */
+int hodlr_autotune(hodlr_ctx* h, int enable);
+/* The remembered plans: up to cap rows of 13 int64 each into out (M, N, K, batch, tA, tB, A
+ * shared, B shared, bmap, beta mode 0/1/2 for 0/1/other; path 0 planes / 1 fused, tile,
+ * chunk multiplier); *n_out = the number of rows in the table (may exceed cap).  */
+int hodlr_autotune_table(int64_t* out, int cap, int* n_out);
+/* Forgets every remembered plan (products fall back to the default plans).  */
+int hodlr_autotune_clear(void);
+
 /* Failure-detection hook (the paper has no counterpart; for tests of the bounded waits).
  * Sets, on the current device, how many times each tensor-core CTA polls its FIRST operand
  * barrier before giving up (polls < 0 restores the default of 2^22 polls).  A CTA whose

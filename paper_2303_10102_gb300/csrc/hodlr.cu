@@ -82,6 +82,7 @@ struct Base {
   virtual void eval_graph(const double* theta, const double* y) = 0;
   virtual const double* graph_out() const = 0;
   uint64_t serial = 0;                       // unique per context (graph cache keys)
+  bool tune = false;                         // tile autotuner on for this context's products
   bool uses_slices = false;                  // HODLR_MIXED_BF16 context
   // N: rows of the (padded) tree layout; Nr: rows of K (natural order).  An uneven cluster
   // tree (median splits of a size that is not leaf x 2^tau) is laid out with every leaf in a
@@ -125,6 +126,7 @@ struct Engine : Base {
   Scratch ozwork, ozsplit;
   void oz_enter(bool on) override {
     g_oz_cfg.on = on && oz;
+    g_oz_cfg.tune = on && oz && tune && !graph_mode;
     g_oz_cfg.work = on && oz ? ozwork : Scratch{};
     g_oz_cfg.split = on && oz ? ozsplit : Scratch{};
   }
@@ -1902,6 +1904,20 @@ int hodlr_batch_nll_grad(hodlr_ctx* const* hs, int nb, const double* thetas, con
     nll_out[i] = out[6 * (size_t)i];
     for (int j = 0; j < 4; ++j) grad_out[4 * (size_t)i + j] = out[6 * (size_t)i + 1 + j];
   }
+  return HODLR_OK;
+}
+int hodlr_autotune(hodlr_ctx* h, int enable) {
+  if (!h || !h->e) return HODLR_EINVAL;
+  h->e->tune = enable != 0;
+  return HODLR_OK;
+}
+int hodlr_autotune_clear(void) {
+  oz_tuned_clear();
+  return HODLR_OK;
+}
+int hodlr_autotune_table(int64_t* out, int cap, int* n_out) {
+  if (!n_out || cap < 0 || (cap > 0 && !out)) return HODLR_EINVAL;
+  *n_out = oz_tuned_table(out, cap);
   return HODLR_OK;
 }
 int hodlr_perm(const hodlr_ctx* h, int64_t* perm_out) {

@@ -65,6 +65,7 @@ bool tf32x3_gemm_nn(const GemmArgs& g, cudaStream_t st);
 // Returns false (nothing launched) for shapes it does not take.
 struct OzConfig {
   bool on = false;
+  bool tune = false;   // time the candidate plans of products not yet tuned (tile autotuner)
   Scratch work;    // slice planes and exponents
   Scratch split;   // split-K partials (used when larger than the caller's scratch)
 };
@@ -72,7 +73,11 @@ extern thread_local OzConfig g_oz_cfg;
 bool oz_eligible(const GemmArgs& g);
 bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st);
 bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st);   // without the size thresholds
-int oz_status_take(cudaStream_t st);   // HODLR_ETIMEOUT recorded by a product (and cleared), or 0
+int oz_status_take(cudaStream_t st);
+// the autotuner's remembered plans: up to cap rows of 13 (shape key of 10, path, tile, chunk
+// multiplier) into out; returns the number of rows in the table
+int oz_tuned_table(int64_t* out, int cap);
+void oz_tuned_clear();   // HODLR_ETIMEOUT recorded by a product (and cleared), or 0
 // Ordered reduction of FP32 split-K partials into C (alpha, beta, offsets as in g).
 void splitk_reduce_f32(const GemmArgs& g, int nsplit, const float* part, cudaStream_t st);
 // hi = x with the low 13 mantissa bits cleared, lo = x - hi (exact); hi may alias x.

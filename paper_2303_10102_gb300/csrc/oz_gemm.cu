@@ -34,7 +34,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "../../include/hodlr.h"
 #include "common.cuh"
@@ -297,6 +300,7 @@ struct OzParams {
                             //    together and read its planes from L2), 0: over M tiles
   const int *exA, *exB;     // exponents [nbA][M], [nbB][N]
   double alpha, beta;
+  int amode, bmode;         // alpha 1 / -1 / other, beta 0 / 1 / other (see oz_out)
   double* C;                // nsplit == 1: C_b = C + b*sC, leading dimension ldc
   long long ldc, sC;
   double* part;             // nsplit > 1: partials ((b*nsplit + s) * M * N) + i + j*M
@@ -327,6 +331,30 @@ __device__ __forceinline__ double oz_i64_to_f64(long long x, int e2) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFULL)));
 }
 
+// round(f 2^sc) for the FP32 value with bits fb (|f 2^sc| < 2^62), by integer operations (a
+// conversion of 64-bit width would run on the FP64 pipes); ties round away from zero
+__device__ __forceinline__ long long oz_f32_scaled_ll(uint32_t fb, int sc) {
+  const int e = (int)((fb >> 23) & 0xffu);
+  if (e == 0) return 0;                                        // zero (or below 2^-126)
+  const long long m = (long long)((fb & 0x7fffffu) | 0x800000u);   // f = m 2^(e - 150)
+  const int sh = e - 150 + sc;
+  long long r;
+  if (sh >= 0) r = m << sh;
+  else if (sh < -25) r = 0;
+  else r = (m + (1LL << (-sh - 1))) >> (-sh);
+  return (fb >> 31) ? -r : r;
+}
+// alpha v + beta c with the modes of alpha (0: 1, 1: -1, 2: other) and beta (0: 0, 1: 1, 2:
+// other) decided on the host: at most one FP64 operation per element (the FP64 pipes of this
+// GPU are slow)
+__device__ __forceinline__ double oz_out(double v, double c, int amode, int bmode, double alpha, double beta) {
+  if (amode == 1) v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+  else if (amode == 2) v *= alpha;
+  if (bmode == 1) return c + v;
+  if (bmode == 2) return fma(beta, c, v);
+  return v;
+}
+
 // One output element from its five accumulators: groups 0..3 hold exact multiples of 2^(-7g)
 // below 2^(24 - 7g), so their values times 2^(7g) are integers that fit 32 bits; they join in
 // V = sum_g acc_g 2^21 (units 2^-21, |V| < 2^43) and, with the tail groups (FP32, below 2^-28 of
@@ -340,7 +368,7 @@ __device__ __forceinline__ double oz_combine(uint32_t a0, uint32_t a1, uint32_t 
   const long long g2 = __float2int_rz(__uint_as_float(a2) * 16384.0f);
   const long long g3 = __float2int_rz(__uint_as_float(a3) * 2097152.0f);
   const long long V = (g0 << 21) + (g1 << 14) + (g2 << 7) + g3;
-  const long long W = (V << 19) + __float2ll_rn(__uint_as_float(at) * 0x1p40f);
+  const long long W = (V << 19) + oz_f32_scaled_ll(at, 40);
   return oz_i64_to_f64(W, ea + eb - 12 - 40);
 }
 
@@ -463,9 +491,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
           const double v = oz_combine(ra[j], rb[j], rc[j], rd[j], rt[j], ea, p.exB[(size_t)bB * p.N + col]);
           if (p.nsplit == 1) {
             double* c = p.C + (size_t)b * p.sC + (size_t)col * p.ldc + row;
-            double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
-            if (p.beta != 0.0) out = p.beta == 1.0 ? *c + out : fma(p.beta, *c, out);
-            *c = out;
+            *c = oz_out(v, p.bmode ? *c : 0.0, p.amode, p.bmode, p.alpha, p.beta);
           } else {
             p.part[((size_t)b * p.nsplit + sp) * ((size_t)p.M * p.N) + (size_t)col * p.M + row] = v;
           }
@@ -646,16 +672,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       if (row < p.M) {
         double* c = p.C + (size_t)b * p.sC + row;
         double cv[16];
-        if (p.beta != 0.0) {
+        if (p.bmode != 0) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) cv[q] = c0 + q < p.N ? c[(size_t)(c0 + q) * p.ldc] : 0.0;
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           if (c0 + q >= p.N) continue;
-          double out = p.alpha == 1.0 ? v[q] : (p.alpha == -1.0 ? -v[q] : p.alpha * v[q]);
-          if (p.beta != 0.0) out = p.beta == 1.0 ? cv[q] + out : fma(p.beta, cv[q], out);
-          c[(size_t)(c0 + q) * p.ldc] = out;
+          c[(size_t)(c0 + q) * p.ldc] = oz_out(v[q], cv[q], p.amode, p.bmode, p.alpha, p.beta);
         }
       }
     }
@@ -760,7 +784,7 @@ __global__ void oz_exp_chunks_kernel(OzView v, int chunk, int nch, int* ex) {
 // contiguous along K (A^T B of column-major operands: the Gram and projection products of the
 // sketch), M <= 128, K long.  A CTA takes BN columns of one product over a range of 512-long
 // chunks of K:
-//   warps 5..12 (producers): read 32-wide slices of the M rows of op(A) and the BN columns of
+//   warps 5..15 (producers): read 32-wide slices of the M rows of op(A) and the BN columns of
 //       op(B) in FP64, cut them into digits with the chunk's exponents and store the 14 planes
 //       of the slice into one of two shared-memory stages;
 //   warp 4 (one thread): the 56 MMAs of each slice into a TMEM accumulator set (two sets used
@@ -773,7 +797,7 @@ __global__ void oz_exp_chunks_kernel(OzView v, int chunk, int nch, int* ex) {
 // follows the plane in shared memory, which reaches only rows of D that are never read.  So do
 // the unwritten rows beyond M and columns beyond N.  Every wait is bounded (abort flag, status
 // HODLR_ETIMEOUT, drain of the issued MMAs before the TMEM is freed).
-constexpr int AT_NPROD = 8;
+constexpr int AT_NPROD = 11;
 constexpr int AT_THREADS = 32 * (5 + AT_NPROD);
 template <int AR, int BN> struct AtTile {
   static constexpr int PLANE_A = AR * 64;                      // bytes per plane and slice
@@ -783,6 +807,8 @@ template <int AR, int BN> struct AtTile {
   static constexpr int SMEM = 2 * STAGE + SUMS + 1024 + 256;
   static constexpr int NSETS = 2 * OZ_NACC * BN <= 512 ? 2 : 1;
   static constexpr int SETW = NSETS == 2 ? 256 : 0;            // TMEM columns between sets
+  // every (row, 8 values) task of a slice has a producer thread, two tasks each
+  static_assert(4 * (AR + BN) <= 2 * 32 * AT_NPROD, "producer threads");
 };
 
 struct AtParams {
@@ -792,6 +818,7 @@ struct AtParams {
   int nch, cpr, nrange;    // 512-long chunks of K; chunks per range; ranges (split of K across CTAs)
   const int *exA, *exB;    // [nbA][nch][M], [nbB][nch][N]
   double alpha, beta;
+  int amode, bmode;        // see oz_out
   double* C;
   long long ldc, sC;
   double* part;            // nrange > 1: partials ((b * nrange + range) * M * N) + i + j * M
@@ -840,52 +867,72 @@ __global__ void __launch_bounds__(AT_THREADS, 1) oz_atb_kernel(const AtParams p)
                          ((uint32_t)(OZ_BM >> 4) << 24);
   int committed = 0;   // MMA progress (slices), for the drain after an abort
   if (warp >= 5) {
-    // ---------------- producers
-    const int ptid = tid - 5 * 32;
+    // ---------------- producers: each thread takes at most two of the slice's (row, 8 values)
+    // tasks; the loads of slice s + 1 are issued before the digits of slice s are made
+    const int ptid = tid - 5 * 32, stride = 32 * AT_NPROD;
     const double* Ab = p.A + (size_t)bA * p.sA;
     const double* Bb = p.B + (size_t)bB * p.sB + (size_t)n0 * p.ldb;
     const int tasks = (p.M + nv) * 4;
+    auto load = [&](int s, int t, double (&x)[8]) {
+      if (t >= tasks) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = 0.0;
+        return -2000;
+      }
+      const int ks = c0 * (OZ_KC / OZ_BK) + s, ch = ks / (OZ_KC / OZ_BK);
+      const int rho = t >> 2, k = ks * OZ_BK + 8 * (t & 3);   // four threads per row: 256 contiguous bytes
+      const double* src;
+      int e;
+      if (rho < p.M) {
+        src = Ab + (size_t)rho * p.lda;
+        e = __ldg(p.exA + ((size_t)bA * p.nch + ch) * p.M + rho);
+      } else {
+        src = Bb + (size_t)(rho - p.M) * p.ldb;
+        e = __ldg(p.exB + ((size_t)bB * p.nch + ch) * p.N + n0 + rho - p.M);
+      }
+      if (k + 8 <= p.K && (((uintptr_t)(src + k)) & 15) == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+          const double2 v = __ldg(reinterpret_cast<const double2*>(src + k + i));
+          x[i] = v.x; x[i + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = k + i < p.K ? __ldg(src + k + i) : 0.0;
+      }
+      return e;
+    };
+    auto store = [&](unsigned char* stg, int t, const double (&x)[8], int e) {
+      const int rho = t >> 2, q = t & 3;
+      if (rho < p.M) oz_put8(x, e, stg, rho, q, TL::PLANE_A);
+      else oz_put8(x, e, stg + OZ_S * TL::PLANE_A, rho - p.M, q, TL::PLANE_B);
+    };
+    double xa[8], xb[8];
+    int ea = load(0, ptid, xa), eb = load(0, ptid + stride, xb);
     for (int s = 0; s < nsl; ++s) {
       if (__any_sync(0xffffffffu, *abort_flag)) break;
+      double ya[8], yb[8];
+      int fa = -2000, fb = -2000;
+      if (s + 1 < nsl) {
+        fa = load(s + 1, ptid, ya);
+        fb = load(s + 1, ptid + stride, yb);
+      }
       const int st = s & 1, u = s >> 1;
       if (u > 0) {
         const bool ok = oz_wait(&empty[st], (u - 1) & 1);
         if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; break; }
       }
-      const int ks = c0 * (OZ_KC / OZ_BK) + s, ch = ks / (OZ_KC / OZ_BK), kb = ks * OZ_BK;
       unsigned char* stg = sm + st * TL::STAGE;
-      for (int t = ptid; t < tasks; t += 32 * AT_NPROD) {
-        const int rho = t >> 2, q = t & 3;   // four threads per row: 256 contiguous bytes
-        const double* src;
-        int e, r, pstride;
-        unsigned char* slice0;
-        if (rho < p.M) {
-          src = Ab + (size_t)rho * p.lda;
-          e = __ldg(p.exA + ((size_t)bA * p.nch + ch) * p.M + rho);
-          slice0 = stg; r = rho; pstride = TL::PLANE_A;
-        } else {
-          r = rho - p.M;
-          src = Bb + (size_t)r * p.ldb;
-          e = __ldg(p.exB + ((size_t)bB * p.nch + ch) * p.N + n0 + r);
-          slice0 = stg + OZ_S * TL::PLANE_A; pstride = TL::PLANE_B;
-        }
-        const int k = kb + 8 * q;
-        double x[8];
-        if (k + 8 <= p.K && (((uintptr_t)(src + k)) & 15) == 0) {
-#pragma unroll
-          for (int i = 0; i < 8; i += 2) {
-            const double2 v = __ldg(reinterpret_cast<const double2*>(src + k + i));
-            x[i] = v.x; x[i + 1] = v.y;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) x[i] = k + i < p.K ? __ldg(src + k + i) : 0.0;
-        }
-        oz_put8(x, e, slice0, r, q, pstride);
-      }
+      if (ptid < tasks) store(stg, ptid, xa, ea);
+      if (ptid + stride < tasks) store(stg, ptid + stride, xb, eb);
       oz_fence_async_smem();
       __syncwarp();
       if (lane == 0) oz_arrive(&full[st]);
+      if (s + 1 < nsl) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { xa[i] = ya[i]; xb[i] = yb[i]; }
+        ea = fa; eb = fb;
+      }
     }
   } else if (warp == 4) {
     if (lane == 0) {
@@ -971,9 +1018,7 @@ __global__ void __launch_bounds__(AT_THREADS, 1) oz_atb_kernel(const AtParams p)
       const double v = sums[i];
       if (p.nrange == 1) {
         double* c = p.C + (size_t)b * p.sC + (size_t)(n0 + col) * p.ldc + row;
-        double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
-        if (p.beta != 0.0) out = p.beta == 1.0 ? *c + out : fma(p.beta, *c, out);
-        *c = out;
+        *c = oz_out(v, p.bmode ? *c : 0.0, p.amode, p.bmode, p.alpha, p.beta);
       } else {
         p.part[((size_t)b * p.nrange + range) * ((size_t)p.M * p.N) + (size_t)(n0 + col) * p.M + row] = v;
       }
@@ -1014,6 +1059,7 @@ struct AbParams {
   int ntm, ntn, ntiles;   // 128-row tiles per product, 48-column subtiles, tiles in all
   const int *exA, *exB;   // [nbA][M], [nbB][N]
   double alpha, beta;
+  int amode, bmode;       // see oz_out
   double* C;
   long long ldc, sC;
 };
@@ -1075,16 +1121,22 @@ __global__ void __launch_bounds__(AB_THREADS, 1)
       const int b = t / p.ntm, m0 = (t % p.ntm) * OZ_BM;
       const int bA = p.nbA == 1 ? 0 : b;
       const double* Ab = p.A + (size_t)bA * p.sA;
-      const int tasks = OZ_BM * (p.Kp / 8);
-      for (int u = ptid; u < tasks; u += 32 * AB_NPROD) {
+      // two tasks per round: their 16 loads are in flight together
+      const int tasks = OZ_BM * (p.Kp / 8), stride = 32 * AB_NPROD;
+      auto load = [&](int u, double (&x)[8]) {
         const int r = u % OZ_BM, qq = u / OZ_BM;   // lanes on consecutive rows
         const int row = m0 + r, k0 = 8 * qq;
-        const bool live = row < p.M;
-        const int e = live ? __ldg(p.exA + (size_t)bA * p.M + row) : -2000;
-        double x[8];
+        const bool live = u < tasks && row < p.M;
 #pragma unroll
         for (int i = 0; i < 8; ++i) x[i] = live && k0 + i < p.K ? __ldg(Ab + row + (size_t)(k0 + i) * p.lda) : 0.0;
-        oz_put8(x, e, abuf + (qq >> 2) * OZ_PLANE_A, r, qq & 3, AB_APLANE);
+        return live ? __ldg(p.exA + (size_t)bA * p.M + row) : -2000;
+      };
+      for (int u = ptid; u < tasks; u += 2 * stride) {
+        double x[8], y[8];
+        const int ex = load(u, x), ey = load(u + stride, y);
+        oz_put8(x, ex, abuf + ((u / OZ_BM) >> 2) * OZ_PLANE_A, u % OZ_BM, (u / OZ_BM) & 3, AB_APLANE);
+        const int u2 = u + stride;
+        if (u2 < tasks) oz_put8(y, ey, abuf + ((u2 / OZ_BM) >> 2) * OZ_PLANE_A, u2 % OZ_BM, (u2 / OZ_BM) & 3, AB_APLANE);
       }
       oz_fence_async_smem();
       __syncwarp();
@@ -1165,21 +1217,17 @@ __global__ void __launch_bounds__(AB_THREADS, 1)
       for (int n = 0; n < p.ntn; ++n, ++jt) {
         const int a = jt & 1;
         const int c0 = n * AB_BN + (AB_BN / 2) * wh;
-        double cv[8], cn[8];
+        // the C values of this warp's 24 columns, loaded before the accumulators are waited for
+        double cv[AB_BN / 2];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          cv[q] = p.beta != 0.0 && live && c0 + q < p.N ? crow[(size_t)(c0 + q) * p.ldc] : 0.0;
+        for (int q = 0; q < AB_BN / 2; ++q)
+          cv[q] = p.bmode && live && c0 + q < p.N ? crow[(size_t)(c0 + q) * p.ldc] : 0.0;
         const bool ok = oz_wait(&accf[a], (jt >> 1) & 1);
         if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; stop = true; break; }
         oz_fence_after();
 #pragma unroll
         for (int h = 0; h < AB_BN / 16; ++h) {
           const int cc = c0 + 8 * h;
-          if (h + 1 < AB_BN / 16) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              cn[q] = p.beta != 0.0 && live && cc + 8 + q < p.N ? crow[(size_t)(cc + 8 + q) * p.ldc] : 0.0;
-          }
           uint32_t ra[8], rb[8], rc[8], rd[8], rt[8];
           const uint32_t base = tmem + lanes + (uint32_t)(256 * a + (AB_BN / 2) * wh + 8 * h);
           oz_ld8(base, ra);
@@ -1200,13 +1248,9 @@ __global__ void __launch_bounds__(AB_THREADS, 1)
               const int col = cc + q;
               if (col >= p.N) continue;
               const double v = oz_combine(ra[q], rb[q], rc[q], rd[q], rt[q], ea, __ldg(p.exB + (size_t)bB * p.N + col));
-              double out = p.alpha == 1.0 ? v : (p.alpha == -1.0 ? -v : p.alpha * v);
-              if (p.beta != 0.0) out = p.beta == 1.0 ? cv[q] + out : fma(p.beta, cv[q], out);
-              crow[(size_t)col * p.ldc] = out;
+              crow[(size_t)col * p.ldc] = oz_out(v, cv[8 * h + q], p.amode, p.bmode, p.alpha, p.beta);
             }
           }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) cv[q] = cn[q];
         }
       }
       if (stop) break;
@@ -1323,6 +1367,9 @@ static size_t oz_bytes(int nbA, int M, int nbB, int N, int Kp) {
          align256((size_t)nbA * M * 4) + align256((size_t)nbB * N * 4);
 }
 
+static int oz_amode(double a) { return a == 1.0 ? 0 : (a == -1.0 ? 1 : 2); }
+static int oz_bmode(double b) { return b == 0.0 ? 0 : (b == 1.0 ? 1 : 2); }
+
 static int oz_num_sms() {
   static int n = 0;
   if (!n) {
@@ -1354,7 +1401,7 @@ struct OzProf {   // CUDA events around a product launch (the context's profile)
 // The fused products (digits made in shared memory by the product kernel): long-K A^T B with
 // M <= 128, and short-K A B with column-major A and K <= 64.  False when the shape is not one of
 // them or its exponents (and the B planes of a short-K product) do not fit the workspace.
-static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st) {
+static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st, int tile, int cprx) {
   const Scratch w = g_oz_cfg.work;
   const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
   const int nb = g.batch;
@@ -1364,7 +1411,7 @@ static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st) {
   const int bmap = sharedB ? BMAP_ID : g.bmap;
   if (g.tA && !g.tB && g.M <= OZ_BM && Kp >= 2 * OZ_KC && nb <= 65535) {
     const int nch = cdiv(Kp, OZ_KC);
-    const bool small = g.M <= 64;
+    const bool small = g.M <= 64 && tile == 0;
     const int bn = small ? 80 : 48;
     const int nparts = cdiv(g.N, bn);
     const size_t ea_bytes = align256((size_t)nbA * nch * g.M * 4);
@@ -1373,7 +1420,7 @@ static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st) {
     int* eB = (int*)((char*)w.ptr + ea_bytes);
     // ranges of chunks per CTA: about one CTA per SM over all products and column parts
     const long long tasks = (long long)nb * nparts * nch;
-    int cpr = (int)std::max<long long>(1, (tasks + oz_num_sms() - 1) / oz_num_sms());
+    int cpr = (int)std::max<long long>(1, (tasks + oz_num_sms() - 1) / oz_num_sms()) * std::max(1, cprx);
     int nrange = cdiv(nch, cpr);
     while (nrange > 1 && (size_t)nb * nrange * g.M * g.N * 8 > split.bytes) {
       cpr *= 2;
@@ -1392,6 +1439,7 @@ static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st) {
     p.M = g.M; p.N = g.N; p.K = g.K; p.nbA = nbA; p.nbB = nbB; p.bmap = bmap;
     p.nch = nch; p.cpr = cpr; p.nrange = nrange;
     p.exA = eA; p.exB = eB; p.alpha = g.alpha; p.beta = g.beta;
+    p.amode = oz_amode(g.alpha); p.bmode = oz_bmode(g.beta);
     p.C = (double*)g.C; p.ldc = g.ldc; p.sC = g.sC; p.part = (double*)split.ptr;
     const dim3 grid(nparts, nrange, nb);
     OzProf prof(st);
@@ -1437,6 +1485,7 @@ static bool oz_fused(const GemmArgs& g, Scratch split, cudaStream_t st) {
     if (ntiles > 0x7fffffffLL) return false;
     p.ntiles = (int)ntiles;
     p.exA = eA; p.exB = eB; p.alpha = g.alpha; p.beta = g.beta;
+    p.amode = oz_amode(g.alpha); p.bmode = oz_bmode(g.beta);
     p.C = (double*)g.C; p.ldc = g.ldc; p.sC = g.sC;
     const int ctas = (int)std::min<long long>(ntiles, oz_num_sms());
     OzProf prof(st);
@@ -1454,9 +1503,8 @@ bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st) {
   return oz_gemm_any(g, split, st);
 }
 
-bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
-  if (!g_oz_cfg.work.ptr || g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
-  if (oz_fused(g, split, st)) return true;
+// the products from slice planes in the workspace (oz_mma_kernel / oz_mma_ws_kernel)
+static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st) {
   const Scratch w = g_oz_cfg.work;
   const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
   const size_t nsp = (size_t)cdiv(Kp, OZ_KC);   // one 512-long chunk of K per CTA
@@ -1495,7 +1543,7 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
       h.A = (const double*)g.A + (g.tA ? (size_t)k0 : (size_t)k0 * g.lda);
       h.B = (const double*)g.B + (g.tB ? (size_t)k0 * g.ldb : (size_t)k0);
       if (k0 > 0) h.beta = 1.0;
-      if (!oz_gemm_any(h, split, st)) throw Error(HODLR_ECUDA, "oz_gemm: K range did not fit");
+      if (!oz_sliced(h, split, st)) throw Error(HODLR_ECUDA, "oz_gemm: K range did not fit");
     }
     return true;
   }
@@ -1547,6 +1595,7 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
       p.M = g.M; p.N = nc; p.K = g.K; p.Kp = Kp; p.nbA = nbA; p.nbB = nbB;
       p.bmap = sharedB ? BMAP_ID : g.bmap; p.nsplit = nsplit;
       p.exA = eA; p.exB = eB; p.alpha = g.alpha; p.beta = g.beta;
+      p.amode = oz_amode(g.alpha); p.bmode = oz_bmode(g.beta);
       p.C = (double*)g.C + (size_t)b0 * g.sC + (size_t)j0 * g.ldc; p.ldc = g.ldc; p.sC = g.sC;
       p.part = (double*)split.ptr;
       if ((long long)nb * nsplit > 65535) throw Error(HODLR_EINVAL, "oz_gemm: batch too large");
@@ -1584,6 +1633,130 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
     }
   }
   return true;
+}
+
+// ---------------------------------------------------------------- tile autotuner
+// A product runs either from slice planes (path 0) or fused (path 1; tile 0: 64 x 80 for M <= 64
+// else 128 x 48, tile 1: 128 x 48; cprx: chunks of K per CTA times the default).  The default
+// plan is the fused path where the shape allows it.  A context with tuning on times, on the
+// first occurrence of a shape, every candidate plan once (after a warm-up run, CUDA events on
+// the context's stream, into a scratch C carved from the slice workspace so that the real C is
+// untouched) and remembers the fastest for the process; the product itself then runs with it.
+struct OzPlan {
+  int path, tile, cprx;
+};
+using OzKey = std::array<long long, 10>;
+static std::mutex g_tune_mu;
+static std::map<OzKey, OzPlan> g_tuned;
+
+static OzKey oz_key(const GemmArgs& g) {
+  return {g.M, g.N, g.K, g.batch, g.tA, g.tB, g.sA == 0, g.sB == 0, g.bmap, oz_bmode(g.beta)};
+}
+// 1: long-K fused shape, 2: short-K fused shape, 0: neither (the conditions of oz_fused)
+static int oz_fused_kind(const GemmArgs& g) {
+  const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  if (g.tA && !g.tB && g.M <= OZ_BM && Kp >= 2 * OZ_KC && g.batch <= 65535) return 1;
+  if (!g.tA && Kp <= AB_KMAX && g.M >= OZ_BM && (long long)g.M * g.batch >= 4096) return 2;
+  return 0;
+}
+static bool oz_run(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan pl) {
+  if (pl.path == 1 && oz_fused(g, split, st, pl.tile, pl.cprx)) return true;
+  return oz_sliced(g, split, st);
+}
+static OzPlan oz_tune(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan def) {
+  std::vector<OzPlan> cand{{0, 0, 1}};
+  const int kind = oz_fused_kind(g);
+  if (kind == 1) {
+    cand.push_back({1, 0, 1});
+    cand.push_back({1, 0, 4});
+    if (g.M <= 64) cand.push_back({1, 1, 1});
+  } else if (kind == 2) {
+    cand.push_back({1, 0, 1});
+  }
+  if (cand.size() == 1) return cand[0];
+  const Scratch w = g_oz_cfg.work;
+  const size_t cbytes = align256((size_t)g.batch * g.M * g.N * sizeof(double));
+  if (cbytes > w.bytes / 2) return def;
+  GemmArgs h = g;
+  h.C = (char*)w.ptr + (w.bytes - cbytes);
+  h.ldc = g.M;
+  h.sC = (long long)g.M * g.N;
+  const OzConfig saved = g_oz_cfg;
+  const bool prof_on = g_prof.on;
+  g_oz_cfg.work.bytes = (w.bytes - cbytes) & ~(size_t)255;
+  g_oz_cfg.tune = false;
+  g_prof.on = false;   // the trial runs stay out of the kernel profile
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  OzPlan best = def;
+  try {
+    HODLR_CUDA(cudaMemsetAsync(h.C, 0, cbytes, st));
+    HODLR_CUDA(cudaEventCreate(&e0));
+    HODLR_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (const OzPlan& c : cand) {
+      if (!oz_run(h, split, st, c)) continue;   // warm-up
+      HODLR_CUDA(cudaEventRecord(e0, st));
+      oz_run(h, split, st, c);
+      oz_run(h, split, st, c);
+      HODLR_CUDA(cudaEventRecord(e1, st));
+      HODLR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      HODLR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+  } catch (...) {
+    g_oz_cfg = saved;
+    g_prof.on = prof_on;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    throw;
+  }
+  g_oz_cfg = saved;
+  g_prof.on = prof_on;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
+  if (!g_oz_cfg.work.ptr || g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
+  OzPlan plan{oz_fused_kind(g) ? 1 : 0, 0, 1};
+  const OzKey key = oz_key(g);
+  bool known = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) { plan = it->second; known = true; }
+  }
+  if (!known && g_oz_cfg.tune) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HODLR_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      plan = oz_tune(g, split, st, plan);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[key] = plan;
+    }
+  }
+  return oz_run(g, split, st, plan);
+}
+
+void oz_tuned_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
+}
+
+int oz_tuned_table(int64_t* out, int cap) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int n = 0;
+  for (const auto& kv : g_tuned) {
+    if (out && n < cap) {
+      int64_t* r = out + 13 * (size_t)n;
+      for (int i = 0; i < 10; ++i) r[i] = kv.first[i];
+      r[10] = kv.second.path; r[11] = kv.second.tile; r[12] = kv.second.cprx;
+    }
+    ++n;
+  }
+  return n;
 }
 
 int oz_status_take(cudaStream_t st) {

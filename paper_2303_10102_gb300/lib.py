@@ -66,6 +66,9 @@ SIGNATURES = {
     "hodlr_napply": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "hodlr_profile": (C.c_int, [_P, C.c_int]),
     "hodlr_profile_read": (C.c_int, [_P, _D]),
+    "hodlr_autotune": (C.c_int, [_P, C.c_int]),
+    "hodlr_autotune_table": (C.c_int, [C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int)]),
+    "hodlr_autotune_clear": (C.c_int, []),
     "hodlr_kernel_count": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "hodlr_reset_kernel_count": (C.c_int, [_P]),
     "hodlr_debug_wait_limit": (C.c_int, [C.c_int]),
@@ -278,6 +281,10 @@ class Hodlr:
         self._check(self.lib.hodlr_napply(self.h, v.ctypes.data_as(C.POINTER(C.c_int64))))
         return int(v[0])
 
+    def autotune(self, enable=True):
+        """Tile autotuner for this context's digit-slice products (hodlr_autotune)."""
+        self._check(self.lib.hodlr_autotune(self.h, int(bool(enable))))
+
     def profile(self, enable):
         self._check(self.lib.hodlr_profile(self.h, int(bool(enable))))
 
@@ -299,6 +306,20 @@ class Hodlr:
         if reset:
             self.lib.hodlr_reset_kernel_count(self.h)
         return int(v[0])
+
+
+def autotune_table():
+    """The autotuner's remembered plans, one dict per product shape."""
+    import numpy as np
+    lib = load()
+    n = C.c_int(0)
+    if lib.hodlr_autotune_table(None, 0, C.byref(n)) != 0:
+        raise HodlrError(-1, "hodlr_autotune_table")
+    out = np.zeros((max(n.value, 1), 13), dtype=np.int64)
+    if lib.hodlr_autotune_table(out.ctypes.data_as(C.POINTER(C.c_int64)), out.shape[0], C.byref(n)) != 0:
+        raise HodlrError(-1, "hodlr_autotune_table")
+    keys = ("M", "N", "K", "batch", "tA", "tB", "A_shared", "B_shared", "bmap", "beta_mode", "path", "tile", "cprx")
+    return [dict(zip(keys, (int(v) for v in row))) for row in out[:n.value]]
 
 
 def from_workload(w, device="cuda", precision=None):

@@ -147,3 +147,16 @@ def test_create_argument_errors_before_device_work(so_path):
                             1 << 30) == -1
     assert lib.hodlr_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(o), None, None, 1 << 30) == -1
     assert not h.value
+
+
+def test_autotune_table_and_argument_errors(so_path):
+    """The tuner's table is host data: empty until a context tunes, readable without a GPU."""
+    import numpy as np
+    lib = plib.load()
+    n = ctypes.c_int(-1)
+    assert lib.hodlr_autotune_clear() == 0
+    assert lib.hodlr_autotune_table(None, 0, ctypes.byref(n)) == 0 and n.value == 0
+    assert lib.hodlr_autotune_table(None, 4, ctypes.byref(n)) == -1
+    assert lib.hodlr_autotune_table(None, 0, None) == -1
+    assert lib.hodlr_autotune(None, 1) == -1
+    assert plib.autotune_table() == []
