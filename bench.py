@@ -283,6 +283,19 @@ def measure_peaks():
     return out
 
 
+# DRAM traffic of one representative launch per kernel family, from a single ncu capture of the
+# current kernels (dram__bytes_read.sum + dram__bytes_write.sum), with the algorithmic FP64
+# operand bytes of the same launch; the summaries under profiles/ give the commands.
+NCU_TRAFFIC = {
+    "oz_mma_kernel": {"bytes": 477.7e6, "algorithmic_bytes": 412.1e6, "shape": "1024 x 16416 x 1024 (DST), beta 1",
+                      "profile": "profiles/oz_mma_kernel_dst_1024x16416x1024.md"},
+    "oz_atb_kernel": {"bytes": 213.2e6, "algorithmic_bytes": 209.9e6, "shape": "64 x 136 x 131072 (A^T B), beta 1",
+                      "profile": "profiles/oz_atb_kernel_long_k_64x136x131072.md"},
+    "oz_ab_kernel": {"bytes": 297.4e6, "algorithmic_bytes": 352.4e6, "shape": "131072 x 136 x 64 (A B), beta 1",
+                     "profile": "profiles/oz_ab_kernel_short_k_131072x136x64.md"},
+}
+
+
 def roofline_entry(prof, ms_step, steps, pk, prec, live_peaks=None):
     """Roofline of the kernel family with the most time in the timed region (CUDA events on the
     context's stream around every product launch)."""
@@ -302,7 +315,8 @@ def roofline_entry(prof, ms_step, steps, pk, prec, live_peaks=None):
         t_hbm = fd.get("bytes", 0.0) / (pk["hbm_gbs"] * 1e9)
         if t_hbm > t_tensor and sec > 0:
             return {"bound": "hbm", "kernel": dom, "achieved": fd["bytes"] / sec / 1e9, "peak": pk["hbm_gbs"],
-                    "unit": "GB/s", "frac": t_hbm / sec, "traffic": None,
+                    "unit": "GB/s", "frac": t_hbm / sec,
+                    "traffic": NCU_TRAFFIC.get(dom, {}).get("bytes"), "traffic_launch": NCU_TRAFFIC.get(dom),
                     "peak_source": ("measured copy bandwidth (MEASURED_PEAKS.json); achieved counts the FP64 operand "
                                     "bytes of the products (A, B once; C read and written) (of measured)"),
                     "tensor_frac": t_tensor / sec,
@@ -330,7 +344,9 @@ def roofline_entry(prof, ms_step, steps, pk, prec, live_peaks=None):
         note = "FP32 FFMA peak measured in this run (hodlr_peak)"
         bound = "alu"
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak_v, "unit": "TFLOP/s",
-            "frac": achieved / peak_v if peak_v else None, "traffic": None, "peak_source": note + " (of measured)",
+            "frac": achieved / peak_v if peak_v else None,
+            "traffic": NCU_TRAFFIC.get(dom, {}).get("bytes"), "traffic_launch": NCU_TRAFFIC.get(dom),
+            "peak_source": note + " (of measured)",
             "kernel_share_of_step": fd["ms"] / steps / ms_step if ms_step else None,
             "launches": fd["launches"] // max(steps, 1),
             "families_ms_per_step": {k: v["ms"] / steps for k, v in fams.items()}}

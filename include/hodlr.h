@@ -182,6 +182,13 @@ int hodlr_probe(hodlr_ctx* h, int level, int ncols, double* out);
  * FP64 device buffer (small N only; for tests).  Needs a prior build.  */
 int hodlr_densify(hodlr_ctx* h, int which, double* out);
 
+/* HODLR product (Table "HODLR operations", Sec. 3.1: the matrix-vector product of the
+ * hierarchical form): Y = K~ X (which = 0) or K~_j X (which = 1..4 for sigma2, ell, kappa,
+ * tau2; K~_sigma2 = (K~ - tau2 I) / sigma2 and K~_tau2 = I, Sec. 3.3) with the matrices of the
+ * last build.  X, Y: device FP64, N x ncols column-major, natural order; Y may not overlap X.
+ * HODLR_EINVAL without a build.  Synchronises the context's stream.  */
+int hodlr_matvec(hodlr_ctx* h, int which, const double* X, double* Y, int ncols);
+
 /* K~^{-1} b in natural order (device FP64 vectors of length N) and log|K~| (host).  */
 int hodlr_solve(hodlr_ctx* h, const double* b, double* x);
 int hodlr_logdet(hodlr_ctx* h, double* logdet_out);

@@ -64,6 +64,7 @@ struct Base {
   virtual void probe(int level, int ncols, double* out) = 0;
   virtual void densify(int which, double* out) = 0;
   virtual void solve_nat(const double* b, double* x) = 0;
+  virtual void matvec_nat(int which, const double* X, double* Y, int ncols) = 0;
   virtual void traces(double* t, double* f) = 0;
   virtual void set_pivots(const int32_t* piv) = 0;
   virtual void logdet_levels(double* out) = 0;
@@ -1436,6 +1437,28 @@ struct Engine : Base {
     HODLR_CUDA(cudaMemcpyAsync(out, res + 60, sizeof(double) * (tau + 1), cudaMemcpyDeviceToHost, st));
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
+  // Y = K~ X (which 0) or K~_j X (which 1..4: sigma2, ell, kappa, tau2), natural order
+  void matvec_nat(int which, const double* X, double* Y, int ncols) override {
+    if (!built) throw Error(HODLR_EINVAL, "no build");
+    const int j = which == 0 || which == 1 || which == 4 ? -1 : which - 2;
+    const int qd = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)wide * sizeof(T) / sizeof(double)));
+    double* Xp = (double*)WZ;
+    double* Yp = (double*)WP;
+    for (int c0 = 0; c0 < ncols; c0 += qd) {
+      const int qq = std::min(qd, ncols - c0);
+      permute_rows<double, double>(X + (size_t)c0 * Nr, Nr, Xp, N, d_perm_plain, N, qq, 0, st);   // padding rows 0
+      if (which == 4) {
+        HODLR_CUDA(cudaMemcpyAsync(Yp, Xp, sizeof(double) * (size_t)N * qq, cudaMemcpyDeviceToDevice, st));
+      } else {
+        matvec<double>(j, (const double*)Xp, N, Yp, N, qq, 0);
+        // K~_sigma2 = (K~ - tau2 I) / sigma2
+        if (which == 1) axpby<double>(N, qq, -theta_built[3] / theta_built[0], (const double*)Xp, N,
+                                      1.0 / theta_built[0], Yp, N, st);
+      }
+      permute_rows<double, double>(Yp, N, Y + (size_t)c0 * Nr, Nr, d_perm_plain, N, qq, 1, st);
+    }
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
   void solve_nat(const double* b, double* x) override {
     if (!built) throw Error(HODLR_EINVAL, "no build");
     permute_rows<double, double>(b, Nr, vec_d, N, d_perm_plain, N, 1, 0, st);
@@ -1963,6 +1986,11 @@ int hodlr_probe(hodlr_ctx* h, int level, int ncols, double* out) {
 int hodlr_densify(hodlr_ctx* h, int which, double* out) {
   if (!out || which < 0 || which > 4) return HODLR_EINVAL;
   return guarded(h, [&] { h->e->densify(which, out); });
+}
+int hodlr_matvec(hodlr_ctx* h, int which, const double* X, double* Y, int ncols) {
+  if (!X || !Y || which < 0 || which > 4 || ncols < 0) return HODLR_EINVAL;
+  if (ncols == 0) return HODLR_OK;
+  return guarded(h, [&] { h->e->matvec_nat(which, X, Y, ncols); });
 }
 int hodlr_solve(hodlr_ctx* h, const double* b, double* x) {
   if (!b || !x) return HODLR_EINVAL;

@@ -59,6 +59,7 @@ SIGNATURES = {
     "hodlr_probe": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "hodlr_densify": (C.c_int, [_P, C.c_int, _P]),
     "hodlr_solve": (C.c_int, [_P, _P, _P]),
+    "hodlr_matvec": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "hodlr_logdet": (C.c_int, [_P, _D]),
     "hodlr_traces": (C.c_int, [_P, _D, _D]),
     "hodlr_logdet_levels": (C.c_int, [_P, _D]),
@@ -250,6 +251,17 @@ class Hodlr:
         x = self.torch.empty_like(bd)
         self._check(self.lib.hodlr_solve(self.h, _P(bd.data_ptr()), _P(x.data_ptr())))
         return x
+
+    def matvec(self, X, which=0):
+        """K~ X (which 0 or "K") or K~_j X (1..4 or the parameter's name) of the last build;
+        X: N or N x ncols (natural order, any device); returns a device tensor of X's shape."""
+        w = WHICH.get(which, which)
+        Xd = self._dev(X)
+        cols = 1 if Xd.dim() == 1 else Xd.shape[1]
+        Xc = Xd.reshape(-1, cols).t().contiguous()        # column-major N x ncols
+        Y = self.torch.empty_like(Xc)
+        self._check(self.lib.hodlr_matvec(self.h, int(w), _P(Xc.data_ptr()), _P(Y.data_ptr()), int(cols)))
+        return Y.t().reshape(Xd.shape)
 
     def logdet(self):
         out = np.zeros(1)

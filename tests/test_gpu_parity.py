@@ -132,6 +132,13 @@ def test_fp64_construction_matches_oracle(name):
         assert rel(h.densify(which).cpu().numpy(), H.densify(which)) < 1e-10, which
     for which in ("ell", "kappa"):
         assert rel(h.densify(which).cpu().numpy(), H.densify(which)) < 1e-7, which
+    # the HODLR product of the API (natural order) against the oracle's densified K~, K~_j
+    X = np.random.default_rng(7).standard_normal((t.N, 5))
+    for which in ("K", "sigma2", "tau2", "ell", "kappa"):
+        ref = np.empty_like(X)
+        ref[t.perm] = H.densify(which) @ X[t.perm]
+        Y = h.matvec(X, which).cpu().numpy()
+        assert rel(Y, ref) < (1e-7 if which in ("ell", "kappa") else 1e-10), which
 
 
 @pytest.mark.parametrize("name", list(SMALL))
