@@ -1678,12 +1678,13 @@ static OzPlan oz_tune(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan 
   const size_t cbytes = align256((size_t)g.batch * g.M * g.N * sizeof(double));
   if (cbytes > w.bytes / 2) return def;
   GemmArgs h = g;
-  h.C = (char*)w.ptr + (w.bytes - cbytes);
+  const size_t keep = (w.bytes - cbytes) & ~(size_t)255;   // the scratch C starts 256-byte aligned
+  h.C = (char*)w.ptr + keep;
   h.ldc = g.M;
   h.sC = (long long)g.M * g.N;
   const OzConfig saved = g_oz_cfg;
   const bool prof_on = g_prof.on;
-  g_oz_cfg.work.bytes = (w.bytes - cbytes) & ~(size_t)255;
+  g_oz_cfg.work.bytes = keep;
   g_oz_cfg.tune = false;
   g_prof.on = false;   // the trial runs stay out of the kernel profile
   cudaEvent_t e0 = nullptr, e1 = nullptr;
