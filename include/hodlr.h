@@ -193,6 +193,18 @@ int hodlr_matvec(hodlr_ctx* h, int which, const double* X, double* Y, int ncols)
 int hodlr_solve(hodlr_ctx* h, const double* b, double* x);
 int hodlr_logdet(hodlr_ctx* h, double* logdet_out);
 
+/* Gradient of the NLL by reverse mode through the factorization (the adjoint route of the
+ * differentiability statement of Sec. 3.3): with Kbar = (K~^{-1} - alpha alpha^T) / 2 the adjoint
+ * of the NLL with respect to K~, grad_j = <Kbar, K~_j> is assembled from the adjoints of the
+ * HODLR factors -- Kbar's leaf blocks (from solves with the leaves' identity columns) and, per
+ * level, the adjoint panel K~^{-1} P - alpha (alpha^T P) of the level's factor panel P restricted
+ * to one side of each sibling pair -- contracted with the tangent factors of Alg. 2 (dA_j, dQ_j,
+ * dB~_j); sigma2 and tau2 through K~_sigma2 = (K~ - tau2 I) / sigma2, K~_tau2 = I.  Equal to
+ * hodlr_grad (the exact traces of App. B) up to rounding.  Builds and factors at theta when the
+ * context holds another build.  y: device FP64, natural order; grad_out: host, 4 doubles.
+ * HODLR_ENOTIMPL on a HODLR_MIXED_FP32 context (its factors are FP32).  */
+int hodlr_grad_adjoint(hodlr_ctx* h, const double* theta, const double* y, double* grad_out);
+
 /* Exact traces (App. B.3): t[i] = tr(K~^{-1} M_i), f[3*i+j] = tr(K~^{-1} M_i K~^{-1} M_j)
  * for M = (I, K~_ell, K~_kappa).  t: host 3, f: host 9.  */
 int hodlr_traces(hodlr_ctx* h, double* t_out, double* f_out);

@@ -2,20 +2,18 @@
 
 The paper states that the HODLR construction can be differentiated (Sec. 3.3) and computes
 the score from the derivative matrices K~_j of Alg. 2 with exact traces (Sec. 4.3,
-App. B).  ``hodlr_nll`` exposes that computation to autograd:
+App. B).  ``hodlr_nll`` exposes the likelihood to autograd with a reverse-mode backward:
 
 * forward: L(theta) = N/2 log 2 pi + 1/2 log det K~ + 1/2 y^T K~^{-1} y (eq. log-like
-  approximated), one build and factorization through the C ABI;
-* backward with respect to theta: the score dL/dtheta_j = 1/2 tr(K~^{-1} K~_j)
-  - 1/2 alpha^T K~_j alpha (eq. score approximated), computed in the same call as the
-  forward value by the library (tangent sweeps of Alg. 2 for ell and kappa, closed forms
-  for sigma^2 and tau^2);
+  approximated): one build (with Alg. 2's tangent factors) and one factorization through the
+  C ABI;
+* backward with respect to theta: the adjoint of L with respect to K~, Kbar = (K~^{-1} -
+  alpha alpha^T) / 2, pulled back through the factorization onto the HODLR factors and
+  contracted with their tangents (hodlr_grad_adjoint): the same score as the trace route of
+  eq. score approximated, by the other mode;
 * backward with respect to y: dL/dy = K~^{-1} y, one more solve with the stored factors.
 
-With four parameters the tangent (forward-mode) sweeps cost less than a reverse sweep would,
-and they are the exact derivative of the same K~(theta), so the autograd gradient is the
-library's gradient.  Nothing here computes on the host: every value comes from the CUDA
-library.
+Nothing here computes on the host: every value comes from the CUDA library.
 """
 from __future__ import annotations
 
@@ -27,10 +25,9 @@ class _HodlrNLL(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, y, h):
         th = theta.detach().to("cpu", torch.float64).numpy()
-        nll, grad = h.nll_grad(th, y.detach())
+        nll = h.nll(th, y.detach())
         ctx.h, ctx.th = h, th
         ctx.save_for_backward(y)
-        ctx.grad_theta = torch.as_tensor(np.asarray(grad, dtype=np.float64))
         return torch.tensor(nll, dtype=torch.float64)
 
     @staticmethod
@@ -38,7 +35,10 @@ class _HodlrNLL(torch.autograd.Function):
         (y,) = ctx.saved_tensors
         g_theta = g_y = None
         if ctx.needs_input_grad[0]:
-            g_theta = (gout.to(torch.float64) * ctx.grad_theta)
+            # reverse mode through the factorization, on the build of the forward call (rebuilt
+            # only if the context was used at another theta in between)
+            grad = ctx.h.grad_adjoint(ctx.th, y.detach())
+            g_theta = gout.to(torch.float64) * torch.as_tensor(np.asarray(grad, dtype=np.float64))
         if ctx.needs_input_grad[1]:
             # K~^{-1} y with the factors of this theta: the evaluation rebuilds only if the
             # context was used at another theta in between

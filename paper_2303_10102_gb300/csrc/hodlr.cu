@@ -65,6 +65,7 @@ struct Base {
   virtual void densify(int which, double* out) = 0;
   virtual void solve_nat(const double* b, double* x) = 0;
   virtual void matvec_nat(int which, const double* X, double* Y, int ncols) = 0;
+  virtual void grad_adjoint(const double* y, double* g) = 0;
   virtual void traces(double* t, double* f) = 0;
   virtual void set_pivots(const int32_t* piv) = 0;
   virtual void logdet_levels(double* out) = 0;
@@ -1402,6 +1403,7 @@ struct Engine : Base {
     HODLR_CUDA(cudaStreamSynchronize(st));
   }
   void set_unit(double* col, int c0, int qq);
+  void grad_adjoint(const double* y, double* g) override;
   void debug_level(int what, int level, double* out, int64_t count, int32_t* w_out) override {
     if (!built || level < 1 || level > tau) throw Error(HODLR_EINVAL, "level");
     int wl = w[level];
@@ -1628,6 +1630,291 @@ template <class T> void Engine<T>::sum_doubles_scaled(double* x, int n, double* 
   check_launch("scale_sum");
 }
 
+// ---------------------------------------------------------------- reverse mode through the factorization
+// The gradient of the NLL as the adjoint of the NLL with respect to the HODLR factors contracted
+// with their tangents: dNLL/dtheta_j = <Kbar, K~_j>, Kbar = (K~^{-1} - alpha alpha^T) / 2, alpha =
+// K~^{-1} y.  K~_j is the block-diagonal dA_j plus, per level and sibling pair, the blocks
+// dB~ Q^T + B~ dQ^T (right x left) and their transposes, so
+//   <Kbar, K~_j> = sum_b <Kbar_bb, dA_j,b> + sum_l <Fbar_l, dF_j,l>,
+// where, for the sibling pair (c1, c2) of level l with factors Q (rows of c1) and B~ (rows of c2),
+//   <Kbar, dB~ Q^T + B~ dQ^T> x 2 = <K~^{-1}[c2,c1] Q - a2 a1^T Q, dB~> + <K~^{-1}[c1,c2] B~ - a1 a2^T B~, dQ>
+// (a = alpha).  The blocks of K~^{-1} follow from the stored factorization (App. C): a node's
+// inverse is D^{-1} - U CP U^T with D its children's block diagonal, U = D^{-1} blockdiag(Q, B~)
+// the stored panel and CP = C^{-1} P the stored core.  Hence
+//   (K~^{-1})_bb = A_b^{-1} - sum_l U_l[b] CP_l[s,s] U_l[b]^T            (leaf b, side s at level l)
+//   K~^{-1}[c2,c1] = -U_l[c2] CP_l[2,1] U_l[c1]^T - sum_{l'<l} U_l'[c2] CP_l'[s,s] U_l'[c1]^T
+// and every term is a contraction of small products U_l'[c]^T F_l[c], U_l'[c]^T dF_l[c] of the
+// stored panels: no solves besides alpha.  sigma2 and tau2 use K~_sigma2 = (K~ - tau2 I) / sigma2
+// and K~_tau2 = I, which need tr K~^{-1} (the leaf blocks).
+__device__ double adj_block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+  return r;   // in every thread
+}
+// per sibling pair v of level l: -<C A_c1, B_c2> - <C' A_c2, B_c1> for j = 0, 1 into red[2v + j],
+// with A_c = U_l'[c]^T F_l[c], B_c = U_l'[c]^T dF_j,l[c] (wp x wl each, stride wp*wl per child c) and
+// C, C' the cores: for l' = l the off-diagonal blocks CP_l[2,1], CP_l[1,2] of the pair; for l' < l
+// the diagonal block CP_l'[s,s] of the level-l' pair holding both children (C = C')
+__global__ void adj_pair_kernel(int wp, int wl, bool same, long long m, long long mp, const double* cp,
+                                const double* A, const double* B0, const double* B1, double* red) {
+  __shared__ double sh[32];
+  const int v = blockIdx.x;
+  const long long wpl = (long long)wp * wl, ld2 = 2LL * wp;
+  const double* A1 = A + (2LL * v) * wpl;
+  const double* A2 = A1 + wpl;
+  const double *C1, *C2;   // core applied to A_c1 (paired with B_c2) and to A_c2 (with B_c1)
+  if (same) {
+    const double* base = cp + (long long)v * 4 * wp * wp;
+    C1 = base + wp;             // CP[2,1]: rows wp.., columns 0..
+    C2 = base + wp * ld2;       // CP[1,2]: rows 0.., columns wp..
+  } else {
+    const long long anc = (2LL * v * m) / mp;          // ancestor child block at depth l'
+    const double* base = cp + (anc >> 1) * 4LL * wp * wp + (anc & 1) * (long long)wp * (2 * wp + 1);
+    C1 = base;
+    C2 = base;
+  }
+  double a0 = 0.0, a1 = 0.0;
+  for (long long e = threadIdx.x; e < wpl; e += blockDim.x) {
+    const int r = (int)(e % wp), c = (int)(e / wp);
+    double t1 = 0.0, t2 = 0.0;
+    for (int k = 0; k < wp; ++k) {
+      t1 += C1[r + k * ld2] * A1[k + (long long)c * wp];
+      t2 += C2[r + k * ld2] * A2[k + (long long)c * wp];
+    }
+    a0 += t1 * B0[(2LL * v + 1) * wpl + e] + t2 * B0[(2LL * v) * wpl + e];
+    a1 += t1 * B1[(2LL * v + 1) * wpl + e] + t2 * B1[(2LL * v) * wpl + e];
+  }
+  a0 = adj_block_sum(a0, sh);
+  a1 = adj_block_sum(a1, sh);
+  if (threadIdx.x == 0) {
+    red[2 * v] = -a0;
+    red[2 * v + 1] = -a1;
+  }
+}
+// per sibling pair v: -(a_c1 . b_c2 + a_c2 . b_c1) with a_c = F_l[c]^T alpha_c, b_c = dF_j,l[c]^T
+// alpha_c (wl each per child c) into red[2v + j]
+__global__ void adj_alpha_kernel(int wl, const double* a, const double* b0, const double* b1, double* red) {
+  __shared__ double sh[32];
+  const int v = blockIdx.x;
+  const double* a1 = a + 2LL * v * wl;
+  const double* a2 = a1 + wl;
+  double s0 = 0.0, s1 = 0.0;
+  for (int e = threadIdx.x; e < wl; e += blockDim.x) {
+    s0 += a1[e] * b0[(2LL * v + 1) * wl + e] + a2[e] * b0[2LL * v * wl + e];
+    s1 += a1[e] * b1[(2LL * v + 1) * wl + e] + a2[e] * b1[2LL * v * wl + e];
+  }
+  s0 = adj_block_sum(s0, sh);
+  s1 = adj_block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    red[2 * v] = -s0;
+    red[2 * v + 1] = -s1;
+  }
+}
+// per leaf b: <A_b^{-1}, dA_j,b> (j = 0, 1) and tr A_b^{-1} over the real rows
+template <class T>
+__global__ void adj_leaf_inv_kernel(int leaf, const int* leafreal, const T* Ainv, const T* dA0, const T* dA1,
+                                    double* red) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  const long long nl2 = (long long)leaf * leaf;
+  double a0 = 0.0, a1 = 0.0, tr = 0.0;
+  for (int e = threadIdx.x; e < leaf * leaf; e += blockDim.x) {
+    const double v = (double)Ainv[b * nl2 + e];
+    a0 += v * (double)dA0[b * nl2 + e];
+    a1 += v * (double)dA1[b * nl2 + e];
+    const int i = e % leaf, k = e / leaf;
+    if (i == k && i < leafreal[b]) tr += v;
+  }
+  a0 = adj_block_sum(a0, sh);
+  a1 = adj_block_sum(a1, sh);
+  tr = adj_block_sum(tr, sh);
+  if (threadIdx.x == 0) {
+    red[3 * b] = a0;
+    red[3 * b + 1] = a1;
+    red[3 * b + 2] = tr;
+  }
+}
+// per leaf b: <CP_l[s, s], G_b> with G_b (w x w, stride w*w) and the core of b's level-l pair
+// (2w x 2w, stride 4 w*w), s the side of the pair that b lies in (children of m rows)
+__global__ void adj_cp_kernel(int leaf, int w, long long m, const double* cp, const double* G, double* red) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  const long long child = (long long)b * leaf / m;
+  const int side = (int)(child & 1);
+  const long long pair = child >> 1;
+  const double* C = cp + pair * 4LL * w * w + (long long)side * w * (2 * w + 1);
+  const double* Gb = G + (long long)b * w * w;
+  double a = 0.0;
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+    const int r = e % w, c = e / w;
+    a += C[r + (long long)c * 2 * w] * Gb[e];
+  }
+  a = adj_block_sum(a, sh);
+  if (threadIdx.x == 0) red[b] = a;
+}
+// per leaf b: alpha_b^T dA_j,b alpha_b (j = 0, 1)
+template <class T>
+__global__ void adj_leaf_quad_kernel(int leaf, const double* alpha, const T* dA0, const T* dA1, double* red) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  const long long nl2 = (long long)leaf * leaf;
+  const double* ab = alpha + (size_t)b * leaf;
+  double a0 = 0.0, a1 = 0.0;
+  for (int e = threadIdx.x; e < leaf * leaf; e += blockDim.x) {
+    const int i = e % leaf, k = e / leaf;
+    const double wgt = ab[i] * ab[k];
+    a0 += wgt * (double)dA0[b * nl2 + e];
+    a1 += wgt * (double)dA1[b * nl2 + e];
+  }
+  a0 = adj_block_sum(a0, sh);
+  a1 = adj_block_sum(a1, sh);
+  if (threadIdx.x == 0) {
+    red[2 * b] = a0;
+    red[2 * b + 1] = a1;
+  }
+}
+// out += sum_i x[i * stride], i < n (fixed order)
+__global__ void adj_sum_strided_kernel(const double* x, int n, int stride, double* out) {
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += x[(size_t)i * stride];
+  v = adj_block_sum(v, sh);
+  if (threadIdx.x == 0) *out += v;
+}
+static void sum_doubles_strided_on(const double* x, int n, int stride, double* out, cudaStream_t st) {
+  adj_sum_strided_kernel<<<1, 1024, 0, st>>>(x, n, stride, out);
+  check_launch("adj_sum");
+}
+__global__ void adj_finish_kernel(const double* acc, double nr, double s2, double t2, double* g) {
+  // acc: 0 <A^{-1}, dA_ell>, 1 <A^{-1}, dA_kappa>, 2 tr A^{-1} (real rows), 3 alpha^T dA_ell alpha,
+  // 4 alpha^T dA_kappa alpha, 5 alpha^T y, 6 alpha^T alpha, 7 levels ell, 8 levels kappa,
+  // 9..11 the Woodbury terms of <(K~^{-1})_bb, dA_ell>, <., dA_kappa>, tr
+  if (threadIdx.x != 0) return;
+  const double tr = acc[2] - acc[11];
+  const double gt2 = 0.5 * (tr - acc[6]);
+  g[3] = gt2;
+  g[0] = (0.5 * (nr - acc[5]) - t2 * gt2) / s2;
+  g[1] = 0.5 * (acc[0] - acc[9] - acc[3]) + acc[7];
+  g[2] = 0.5 * (acc[1] - acc[10] - acc[4]) + acc[8];
+}
+
+template <class T> void Engine<T>::grad_adjoint(const double* y_nat, double* g_out) {
+  if (!built) throw Error(HODLR_EINVAL, "no build");
+  if constexpr (sizeof(T) != 8) {
+    throw Error(HODLR_ENOTIMPL, "the adjoint route uses the FP64 factors (HODLR_FP64 or HODLR_MIXED_BF16)");
+  } else {
+    double* alpha = vec_d + N;
+    double* acc = res + 280;       // 12 accumulators (res[280..291]); the result goes to res[300..303]
+    double* yt = vec_d;
+    HODLR_CUDA(cudaMemsetAsync(acc, 0, 12 * sizeof(double), st));
+    permute_rows<double, double>(y_nat, Nr, yt, N, d_perm_plain, N, 1, 0, st);
+    solve64(yt, N, alpha, N, 1, 0);
+    dot_columns<double, double>(N, 1, alpha, N, yt, N, red, st);
+    sum_doubles(red, 1, acc + 5, 1, st);
+    dot_columns<double, double>(N, 1, alpha, N, alpha, N, red, st);
+    sum_doubles(red, 1, acc + 6, 1, st);
+    double* P = (double*)WZ;
+    double* Z = (double*)WP;
+    // leaves
+    adj_leaf_quad_kernel<T><<<nleaves, 256, 0, st>>>(leaf, alpha, dA[0], dA[1], red);
+    check_launch("adj_leaf_quad");
+    for (int k = 0; k < 2; ++k) sum_doubles_strided_on(red + k, nleaves, 2, acc + 3 + k, st);
+    // leaf blocks of K~^{-1}: A_b^{-1} minus the Woodbury terms of every level
+    adj_leaf_inv_kernel<T><<<nleaves, 256, 0, st>>>(leaf, d_leafreal, Ainv, dA[0], dA[1], red);
+    check_launch("adj_leaf_inv");
+    for (int k = 0; k < 3; ++k) sum_doubles_strided_on(red + k, nleaves, 3, acc + k, st);
+    for (int l = 1; l <= tau; ++l) {
+      const int wl = w[l];
+      if (wl == 0) continue;
+      double* T1 = P;                                  // M_b U_l[b], N x wl (leaf rows per leaf)
+      double* Gb = Z;                                  // U_l[b]^T M_b U_l[b], wl x wl per leaf
+      for (int k = 0; k < 3; ++k) {                    // M = dA_ell, dA_kappa, I
+        const double* R = U[l];
+        if (k < 2) {
+          GemmArgs g;
+          g.M = leaf; g.N = wl; g.K = leaf;
+          g.A = dA[k]; g.lda = leaf; g.sA = (long long)leaf * leaf;
+          g.B = U[l]; g.ldb = N; g.sB = leaf;
+          g.C = T1; g.ldc = N; g.sC = leaf; g.batch = nleaves;
+          g64<T, double>(g);
+          R = T1;
+        }
+        GemmArgs h;
+        h.M = wl; h.N = wl; h.K = leaf;
+        h.A = U[l]; h.lda = N; h.sA = leaf; h.tA = 1;
+        h.B = R; h.ldb = N; h.sB = leaf;
+        h.C = Gb; h.ldc = wl; h.sC = (long long)wl * wl; h.batch = nleaves;
+        g64<double, double>(h);
+        adj_cp_kernel<<<nleaves, 256, 0, st>>>(leaf, wl, msize(l), CP64[l], Gb, red);
+        check_launch("adj_cp");
+        sum_doubles_strided_on(red, nleaves, 1, acc + 9 + k, st);   // subtracted at the end
+      }
+    }
+    // sibling pairs of every level: the K~^{-1} blocks of the own level and of every coarser one
+    const size_t blk = (size_t)nleaves * cap * cap;    // one wp x wl product per child block
+    const size_t room = (size_t)N * wide * sizeof(T) / sizeof(double);   // doubles in each wide panel
+    if (2 * blk > room || blk + 3 * (size_t)nleaves * cap > room)
+      throw Error(HODLR_ENOTIMPL, "adjoint route: the rank cap is too large for the wide panels");
+    double* Ab = P;
+    double* B0 = P + blk;
+    double* B1 = Z;
+    for (int l = 1; l <= tau; ++l) {
+      const int wl = w[l];
+      if (wl == 0) continue;
+      const long long m = msize(l);
+      const int nb = 1 << l, np = npairs(l);
+      auto prod = [&](const double* Ul, int wp, const T* R, double* out) {   // U_l'[c]^T R[c] per child c
+        GemmArgs g;
+        g.M = wp; g.N = wl; g.K = (int)m;
+        g.A = Ul; g.lda = N; g.sA = m; g.tA = 1;
+        g.B = R; g.ldb = N; g.sB = m;
+        g.C = out; g.ldc = wp; g.sC = (long long)wp * wl; g.batch = nb;
+        g64<double, T>(g);
+      };
+      for (int lp = 1; lp <= l; ++lp) {
+        const int wp = w[lp];
+        if (wp == 0) continue;
+        prod(U[lp], wp, F[l], Ab);
+        prod(U[lp], wp, dF[0][l], B0);
+        prod(U[lp], wp, dF[1][l], B1);
+        adj_pair_kernel<<<np, 256, 0, st>>>(wp, wl, lp == l, m, msize(lp), CP64[lp], Ab, B0, B1, red);
+        check_launch("adj_pair");
+        for (int k = 0; k < 2; ++k) sum_doubles_strided_on(red + k, np, 2, acc + 7 + k, st);
+      }
+      // the alpha alpha^T part: a_c = F_l[c]^T alpha_c, b_c = dF_j,l[c]^T alpha_c
+      {
+        double* av = Z + blk;
+        double* bv0 = av + (size_t)nb * wl;
+        double* bv1 = bv0 + (size_t)nb * wl;
+        auto vec = [&](const T* R, double* out) {
+          GemmArgs g;
+          g.M = wl; g.N = 1; g.K = (int)m;
+          g.A = R; g.lda = N; g.sA = m; g.tA = 1;
+          g.B = alpha; g.ldb = N; g.sB = m;
+          g.C = out; g.ldc = wl; g.sC = wl; g.batch = nb;
+          g64<T, double>(g);
+        };
+        vec(F[l], av);
+        vec(dF[0][l], bv0);
+        vec(dF[1][l], bv1);
+        adj_alpha_kernel<<<np, 256, 0, st>>>(wl, av, bv0, bv1, red);
+        check_launch("adj_alpha");
+        for (int k = 0; k < 2; ++k) sum_doubles_strided_on(red + k, np, 2, acc + 7 + k, st);
+      }
+    }
+    double* gd = res + 300;
+    adj_finish_kernel<<<1, 32, 0, st>>>(acc, (double)Nr, theta_built[0], theta_built[3], gd);
+    check_launch("adj_finish");
+    HODLR_CUDA(cudaMemcpyAsync(g_out, gd, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HODLR_CUDA(cudaStreamSynchronize(st));
+  }
+}
+
 template struct Engine<double>;
 template struct Engine<float>;
 
@@ -1757,6 +2044,14 @@ int hodlr_nll(hodlr_ctx* h, const double* theta, const double* y, double* nll_ou
 int hodlr_grad(hodlr_ctx* h, const double* theta, const double* y, double* grad_out) {
   if (!theta || !y || !grad_out) return HODLR_EINVAL;
   return guarded(h, [&] { double g[4]; h->e->eval(theta, y, nullptr, g, nullptr); std::memcpy(grad_out, g, sizeof(g)); });
+}
+int hodlr_grad_adjoint(hodlr_ctx* h, const double* theta, const double* y, double* grad_out) {
+  if (!theta || !y || !grad_out) return HODLR_EINVAL;
+  return guarded(h, [&] {
+    double v;
+    h->e->eval(theta, y, &v, nullptr, nullptr);   // build and factor at theta (reused when current)
+    h->e->grad_adjoint(y, grad_out);
+  });
 }
 int hodlr_fisher(hodlr_ctx* h, const double* theta, double* fisher_out) {
   if (!theta || !fisher_out) return HODLR_EINVAL;

@@ -47,6 +47,7 @@ SIGNATURES = {
     "hodlr_build": (C.c_int, [_P, _D, _D]),
     "hodlr_nll": (C.c_int, [_P, _D, _P, _D]),
     "hodlr_grad": (C.c_int, [_P, _D, _P, _D]),
+    "hodlr_grad_adjoint": (C.c_int, [_P, _D, _P, _D]),
     "hodlr_fisher": (C.c_int, [_P, _D, _D]),
     "hodlr_eval": (C.c_int, [_P, _D, _P, _D, _D, _D]),
     "hodlr_batch_nll_grad": (C.c_int, [C.POINTER(_P), C.c_int, _D, C.POINTER(_P), _D, _D]),
@@ -171,6 +172,12 @@ class Hodlr:
     def grad(self, theta, y):
         th, yd, out = self._theta(theta), self._dev(y), np.zeros(4)
         self._check(self.lib.hodlr_grad(self.h, _dp(th), _P(yd.data_ptr()), _dp(out)))
+        return out
+
+    def grad_adjoint(self, theta, y):
+        """The gradient by reverse mode through the factorization (hodlr_grad_adjoint)."""
+        th, yd, out = self._theta(theta), self._dev(y), np.zeros(4)
+        self._check(self.lib.hodlr_grad_adjoint(self.h, _dp(th), _P(yd.data_ptr()), _dp(out)))
         return out
 
     def nll_grad(self, theta, y):

@@ -1,6 +1,6 @@
-"""Host logic of the autograd wrapper (no GPU): the backward pass returns the library's
-gradient scaled by the incoming gradient, and K~^{-1} y for the data, from a stand-in
-context whose values are fixed numbers."""
+"""Host logic of the autograd wrapper (no GPU): forward evaluates the NLL only; the backward
+pass asks the library for the reverse-mode gradient at the forward theta, scaled by the incoming
+gradient, and for K~^{-1} y for the data, from a stand-in context whose values are fixed."""
 import numpy as np
 import torch
 
@@ -14,13 +14,13 @@ class FakeContext:
         self.d = torch.as_tensor(d, dtype=torch.float64)
         self.calls = []
 
-    def nll_grad(self, theta, y):
-        self.calls.append(("nll_grad", tuple(theta)))
-        return float(0.5 * (y * y / self.d).sum() + 3.0), np.array([1.0, -2.0, 0.5, 4.0])
-
     def nll(self, theta, y):
         self.calls.append(("nll", tuple(theta)))
         return float(0.5 * (y * y / self.d).sum() + 3.0)
+
+    def grad_adjoint(self, theta, y):
+        self.calls.append(("grad_adjoint", tuple(theta)))
+        return np.array([1.0, -2.0, 0.5, 4.0])
 
     def solve(self, y):
         self.calls.append(("solve",))
@@ -35,8 +35,10 @@ def test_backward_theta_and_y():
     loss.backward()
     assert torch.equal(theta.grad, torch.tensor([2.0, -4.0, 1.0, 8.0], dtype=torch.float64))
     assert torch.allclose(y.grad, 2.0 * y.detach() / h.d)
-    # the y-gradient re-evaluates at the forward theta before solving
-    assert h.calls[0][0] == "nll_grad" and h.calls[1] == ("nll", (1.0, 0.1, 5.0, 1e-4)) and h.calls[2] == ("solve",)
+    th = (1.0, 0.1, 5.0, 1e-4)
+    # forward: NLL only; backward: the adjoint gradient at the forward theta, then K~^{-1} y
+    assert h.calls[0] == ("nll", th) and h.calls[1] == ("grad_adjoint", th)
+    assert h.calls[2] == ("nll", th) and h.calls[3] == ("solve",)
 
 
 def test_no_solve_without_y_grad():
@@ -44,5 +46,5 @@ def test_no_solve_without_y_grad():
     theta = torch.tensor([1.0, 0.1, 5.0, 1e-4], dtype=torch.float64, requires_grad=True)
     y = torch.tensor([0.5, 0.25], dtype=torch.float64)
     hodlr_nll(h, theta, y).backward()
-    assert [c[0] for c in h.calls] == ["nll_grad"]
+    assert [c[0] for c in h.calls] == ["nll", "grad_adjoint"]
     assert theta.grad is not None

@@ -1,5 +1,6 @@
-"""The differentiable NLL on the GPU: autograd's theta-gradient equals the library's exact
-score and the oracle's; the y-gradient equals K~^{-1} y of the densified oracle K~."""
+"""The differentiable NLL on the GPU: autograd's theta-gradient (reverse mode through the
+factorization) equals the trace-route score of the library, the oracle's score and central
+differences of the GPU NLL; the y-gradient equals K~^{-1} y of the densified oracle K~."""
 import numpy as np
 import pytest
 import torch
@@ -24,8 +25,18 @@ def test_autograd_matches_score_and_oracle():
     y = torch.as_tensor(y_np, device=DEV).requires_grad_(True)
     loss = hodlr_nll(h, theta, y)
     loss.backward()
-    g_lib = h.grad(w.theta, y.detach())
-    assert np.array_equal(theta.grad.numpy(), g_lib)
+    g_lib = h.grad(w.theta, y.detach())                 # forward (tangent) mode, exact traces
+    assert np.array_equal(theta.grad.numpy(), h.grad_adjoint(w.theta, y.detach()))
+    assert np.all(np.abs(theta.grad.numpy() - g_lib) <= 1e-9 * np.abs(g_lib).max())
+    # central differences of the GPU NLL (probes and pivot sets frozen: Sec. 3.3)
+    h.build(w.theta)
+    h.set_pivots(h.get_pivots())
+    for j in range(4):
+        e = np.zeros(4)
+        e[j] = 1e-5 * w.theta[j]
+        fd = (h.nll(np.asarray(w.theta) + e, y.detach()) - h.nll(np.asarray(w.theta) - e, y.detach())) / (2 * e[j])
+        assert abs(fd - theta.grad.numpy()[j]) <= 1e-6 * np.abs(theta.grad.numpy()).max(), (j, fd, theta.grad)
+    h.set_pivots(None)
     H = oh.build(m, t, w.theta, c=12, cap=10, guard=1e-5, seed=1)
     f0, g0, _ = ol.evaluate(H, t.to_tree(y_np))
     assert abs(loss.item() - f0) <= 1e-10 * abs(f0)
