@@ -202,6 +202,27 @@ __device__ __forceinline__ void oz_digits(long long F, int (&d)[OZ_S]) {
   d[OZ_S - 1] = (int)F;
 }
 
+// d 2^(-7p) as BF16 (exact: |d| <= 64 and 2^(-42) is a normal float)
+__device__ __forceinline__ __nv_bfloat16 oz_digit_bf16(int d, int p) {
+  return __float2bfloat16_rn((float)d * __uint_as_float((uint32_t)(127 - 7 * p) << 23));
+}
+// the row exponents of an operand whose rows are contiguous (sr == 1) and long along k: the
+// biased maxima of (row, 64-long piece of k) go into ex by atomicMax (ex zeroed before), then
+// oz_rowexp_fix turns them into exponents; threads of a warp on consecutive rows
+__global__ void oz_rowexp_split_kernel(OzView v, int kc, int* ex) {
+  const int b = blockIdx.z;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= v.R) return;
+  const double* base = v.base + (size_t)b * v.sb + (size_t)r * v.sr;
+  const int k0 = blockIdx.y * kc, k1 = min(v.K, k0 + kc);
+  int m = 0;
+  for (int k = k0; k < k1; ++k) m = max(m, oz_biased_exp(__ldg(base + (size_t)k * v.sk)));
+  if (m) atomicMax(ex + (size_t)b * v.R + r, m);
+}
+__global__ void oz_rowexp_fix_kernel(long long n, int* ex) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) ex[i] = ex[i] == 0 ? -2000 : ex[i] - 1023 + 1;
+}
 // 32 (r) x 32 (k) tiles through shared memory: loads are coalesced along the operand's
 // contiguous direction, plane stores along k
 __global__ void oz_slice_kernel(OzView v, const int* ex, __nv_bfloat16* planes, int Kp) {
@@ -229,7 +250,7 @@ __global__ void oz_slice_kernel(OzView v, const int* ex, __nv_bfloat16* planes, 
     oz_digits(oz_fixed(tile[j][tx], e), d);
     const size_t o = ((size_t)b * v.R + r) * Kp + k;
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) planes[p * plane + o] = __float2bfloat16_rn(ldexpf((float)d[p], -7 * p));
+    for (int p = 0; p < OZ_S; ++p) planes[p * plane + o] = oz_digit_bf16(d[p], p);
   }
 }
 
@@ -253,7 +274,7 @@ __global__ void oz_slice_rows_kernel(OzView v, int* ex, __nv_bfloat16* planes, i
     int d[OZ_S];
     oz_digits(oz_fixed(k < v.K ? row[k] : 0.0, e), d);
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) planes[p * plane + o0 + k] = __float2bfloat16_rn(ldexpf((float)d[p], -7 * p));
+    for (int p = 0; p < OZ_S; ++p) planes[p * plane + o0 + k] = oz_digit_bf16(d[p], p);
   }
 }
 
@@ -285,7 +306,7 @@ __global__ void oz_slice_cols_kernel(OzView v, int* ex, __nv_bfloat16* planes, i
       int d[OZ_S];
       oz_digits(oz_fixed(tile[k][j], se[j]), d);
 #pragma unroll
-      for (int p = 0; p < OZ_S; ++p) planes[p * plane + o0 + k] = __float2bfloat16_rn(ldexpf((float)d[p], -7 * p));
+      for (int p = 0; p < OZ_S; ++p) planes[p * plane + o0 + k] = oz_digit_bf16(d[p], p);
     }
   }
 }
@@ -1333,6 +1354,15 @@ void oz_slice(const OzView& v, int Kp, int* ex, __nv_bfloat16* planes, cudaStrea
   if (v.sk == 1) {
     dim3 g(cdiv(v.R, 8), v.nb);
     oz_rowexp_kernel<<<g, 256, 0, st>>>(v, ex);
+  } else if (v.K > 128) {
+    // many rows of long k: split k across CTAs (one thread per row would leave the GPU idle)
+    HODLR_CUDA(cudaMemsetAsync(ex, 0, sizeof(int) * (size_t)v.nb * v.R, st));
+    const int kc = 64 * (int)cdiv(cdiv(v.K, 64), 65535);   // pieces of k: at most 65535 across the grid
+    dim3 g(cdiv(v.R, 128), cdiv(v.K, kc), v.nb);
+    oz_rowexp_split_kernel<<<g, 128, 0, st>>>(v, kc, ex);
+    check_launch("oz_rowexp");
+    const long long n = (long long)v.nb * v.R;
+    oz_rowexp_fix_kernel<<<cdiv(n, 256), 256, 0, st>>>(n, ex);
   } else {
     dim3 g(cdiv(v.R, 128), v.nb);
     oz_rowexp_kernel<<<g, 128, 0, st>>>(v, ex);
