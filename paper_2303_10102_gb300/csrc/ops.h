@@ -77,7 +77,8 @@ int oz_status_take(cudaStream_t st);
 // the autotuner's remembered plans: up to cap rows of 13 (shape key of 10, path, tile, chunk
 // multiplier) into out; returns the number of rows in the table
 int oz_tuned_table(int64_t* out, int cap);
-void oz_tuned_clear();   // HODLR_ETIMEOUT recorded by a product (and cleared), or 0
+void oz_tuned_clear();
+void oz_force_plan(int path, int tile, int cprx);   // this thread's products (path < 0: automatic)   // HODLR_ETIMEOUT recorded by a product (and cleared), or 0
 // Ordered reduction of FP32 split-K partials into C (alpha, beta, offsets as in g).
 void splitk_reduce_f32(const GemmArgs& g, int nsplit, const float* part, cudaStream_t st);
 // hi = x with the low 13 mantissa bits cleared, lo = x - hi (exact); hi may alias x.

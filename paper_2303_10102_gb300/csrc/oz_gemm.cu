@@ -1534,7 +1534,10 @@ bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st) {
 }
 
 // the products from slice planes in the workspace (oz_mma_kernel / oz_mma_ws_kernel)
-static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st) {
+// tile 0: 128 x 96 tiles, two stages, one CTA per SM; tile 1: 128 x 48 tiles, one stage, two CTAs
+// per SM (one CTA's epilogue overlaps the other's loads and products); K <= 128 always takes the
+// persistent 128 x 32 kernel
+static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st, int tile = 0) {
   const Scratch w = g_oz_cfg.work;
   const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
   const size_t nsp = (size_t)cdiv(Kp, OZ_KC);   // one 512-long chunk of K per CTA
@@ -1573,14 +1576,16 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st) {
       h.A = (const double*)g.A + (g.tA ? (size_t)k0 : (size_t)k0 * g.lda);
       h.B = (const double*)g.B + (g.tB ? (size_t)k0 * g.ldb : (size_t)k0);
       if (k0 > 0) h.beta = 1.0;
-      if (!oz_sliced(h, split, st)) throw Error(HODLR_ECUDA, "oz_gemm: K range did not fit");
+      if (!oz_sliced(h, split, st, tile)) throw Error(HODLR_ECUDA, "oz_gemm: K range did not fit");
     }
     return true;
   }
   // short K (one to four 32-wide slices): the persistent warp-specialised kernel over 128 x 32 tiles
   const bool narrow = Kp <= 4 * OZ_BK;
+  const bool half = !narrow && tile == 1;
   using Wide = OzTile<OZ_BN, 2>;
-  const int bn = narrow ? WS_BN : OZ_BN;
+  using Half = OzTile<OZ_BN / 2, 1>;
+  const int bn = narrow ? WS_BN : (half ? OZ_BN / 2 : OZ_BN);
   static int num_sms = 0;
   if (!num_sms) {
     int dev = 0;
@@ -1588,6 +1593,8 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st) {
     HODLR_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
   if (narrow) HODLR_CUDA(cudaFuncSetAttribute(oz_mma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM));
+  else if (half)
+    HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<OZ_BN / 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Half::SMEM));
   else HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<OZ_BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide::SMEM));
   for (int b0 = 0; b0 < g.batch; b0 += bchunk) {
     const int nb = std::min(bchunk, g.batch - b0);
@@ -1642,7 +1649,8 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st) {
         oz_mma_ws_kernel<<<ctas, WS_THREADS, WS_SMEM, st>>>(ma, mb, p, ntm, ntn, (int)ntiles);
         check_launch("oz_mma_ws_kernel");
       } else {
-        oz_mma_kernel<OZ_BN, 2><<<grid, OZ_THREADS, Wide::SMEM, st>>>(ma, mb, p);
+        if (half) oz_mma_kernel<OZ_BN / 2, 1><<<grid, OZ_THREADS, Half::SMEM, st>>>(ma, mb, p);
+        else oz_mma_kernel<OZ_BN, 2><<<grid, OZ_THREADS, Wide::SMEM, st>>>(ma, mb, p);
         check_launch("oz_mma_kernel");
       }
       if (prof) {
@@ -1666,8 +1674,9 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- tile autotuner
-// A product runs either from slice planes (path 0) or fused (path 1; tile 0: 64 x 80 for M <= 64
-// else 128 x 48, tile 1: 128 x 48; cprx: chunks of K per CTA times the default).  The default
+// A product runs either from slice planes (path 0; tile 0: 128 x 96, tile 1: 128 x 48 with two
+// CTAs per SM) or fused (path 1; tile 0: 64 x 80 for M <= 64 else 128 x 48, tile 1: 128 x 48;
+// cprx: chunks of K per CTA times the default).  The default
 // plan is the fused path where the shape allows it.  A context with tuning on times, on the
 // first occurrence of a shape, every candidate plan once (after a warm-up run, CUDA events on
 // the context's stream, into a scratch C carved from the slice workspace so that the real C is
@@ -1691,10 +1700,11 @@ static int oz_fused_kind(const GemmArgs& g) {
 }
 static bool oz_run(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan pl) {
   if (pl.path == 1 && oz_fused(g, split, st, pl.tile, pl.cprx)) return true;
-  return oz_sliced(g, split, st);
+  return oz_sliced(g, split, st, pl.path == 0 ? pl.tile : 0);
 }
 static OzPlan oz_tune(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan def) {
   std::vector<OzPlan> cand{{0, 0, 1}};
+  if (((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK > 4 * OZ_BK) cand.push_back({0, 1, 1});   // 128 x 48 tiles
   const int kind = oz_fused_kind(g);
   if (kind == 1) {
     cand.push_back({1, 0, 1});
@@ -1749,8 +1759,12 @@ static OzPlan oz_tune(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan 
   return best;
 }
 
+// a plan forced on this thread (hodlr_dgemm_slices_plan; path < 0: automatic)
+static thread_local OzPlan g_forced{-1, 0, 1};
+
 bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
   if (!g_oz_cfg.work.ptr || g.offmode != 0 || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return false;
+  if (g_forced.path >= 0) return oz_run(g, split, st, g_forced);
   OzPlan plan{oz_fused_kind(g) ? 1 : 0, 0, 1};
   const OzKey key = oz_key(g);
   bool known = false;
@@ -1770,6 +1784,8 @@ bool oz_gemm_any(const GemmArgs& g, Scratch split, cudaStream_t st) {
   }
   return oz_run(g, split, st, plan);
 }
+
+void oz_force_plan(int path, int tile, int cprx) { g_forced = OzPlan{path, tile, cprx}; }
 
 void oz_tuned_clear() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1801,6 +1817,12 @@ int oz_status_take(cudaStream_t st) {
 }  // namespace hodlr
 
 using namespace hodlr;
+
+extern "C" int hodlr_dgemm_slices_plan(int path, int tile, int cprx) {
+  if (path < -1 || path > 1 || tile < 0 || tile > 1 || cprx < 1) return HODLR_EINVAL;
+  oz_force_plan(path, tile, cprx);
+  return HODLR_OK;
+}
 
 extern "C" int hodlr_dgemm_slices(int M, int N, int K, int batch, const double* A, long long lda, long long sA,
                                   int tA, const double* B, long long ldb, long long sB, int tB, int bmap,

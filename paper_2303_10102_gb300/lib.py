@@ -78,6 +78,7 @@ SIGNATURES = {
     "hodlr_dgemm_slices": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_longlong, C.c_longlong, C.c_int,
                                      _P, C.c_longlong, C.c_longlong, C.c_int, C.c_int, C.c_double, C.c_double, _P,
                                      C.c_longlong, C.c_longlong, _P, C.c_size_t, _P]),
+    "hodlr_dgemm_slices_plan": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "hodlr_apply_static": (C.c_int, [C.c_int, C.c_double, _D, _P, _P, C.c_int, _P]),
     "hodlr_last_error": (C.c_char_p, [_P]),
     "hodlr_destroy": (None, [_P]),

@@ -240,3 +240,34 @@ def test_fused_long_k_scaled_operands_ragged_and_batched():
         got = C.cpu().numpy().reshape(nb, N, M).transpose(0, 2, 1)
         for b in range(nb):
             assert np.all(np.abs(got[b] - As[b] @ pick(b)) <= 1.5 * _bound(As[b], pick(b))), (bmap, b)
+
+
+@pytest.mark.parametrize("plan", [(0, 0, 1), (0, 1, 1), (1, 0, 1), (1, 1, 1), (1, 0, 4)])
+def test_every_kernel_plan_is_exact_and_accurate(plan):
+    """Each plan the autotuner can choose (slice planes with 128 x 96 or 128 x 48 tiles, fused with
+    either tile and more chunks per CTA), forced for this thread, on a long-K A^T B, a short-K A B
+    and a general A B: integer operands bit-exact, scaled operands within the slicing bound."""
+    from paper_2303_10102_gb300 import lib as plib
+    lib = plib.load()
+    assert lib.hodlr_dgemm_slices_plan(*plan) == 0
+    try:
+        rng = np.random.default_rng(sum(plan))
+        for M, N, K, tA in [(100, 150, 3000, 1), (5000, 70, 40, 0), (300, 200, 700, 0)]:
+            for integer in (True, False):
+                if integer:
+                    A = rng.integers(-1000, 1001, size=(M, K)).astype(np.float64)
+                    B = rng.integers(-1000, 1001, size=(K, N)).astype(np.float64)
+                else:
+                    A = _scaled(rng, M, K)
+                    B = _scaled(rng, K, N)
+                Ast = colmajor(A.T if tA else A)
+                C = torch.zeros(M * N, dtype=torch.float64, device=DEV)
+                assert slices(Ast, colmajor(B), M, N, K, 1, K if tA else M, 0, tA, K, 0, 0, 0, 1.0, 0.0, C, M, 0) == 0
+                got = C.cpu().numpy().reshape(N, M).T
+                if integer:
+                    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+                    assert np.array_equal(got, ref), (plan, M, N, K)
+                else:
+                    assert np.all(np.abs(got - A @ B) <= 1.5 * _bound(A, B)), (plan, M, N, K)
+    finally:
+        lib.hodlr_dgemm_slices_plan(-1, 0, 1)
