@@ -331,25 +331,19 @@ struct OzParams {
 // FP64 pipes of this GPU are slow); results below the normal range flush to zero
 __device__ __forceinline__ double oz_i64_to_f64(long long x, int e2) {
   if (x == 0) return 0.0;
-  const unsigned long long sgn = x < 0 ? 0x8000000000000000ULL : 0ULL;
-  unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
-  const int msb = 63 - __clzll((long long)a);
-  int ex = msb + e2;
-  unsigned long long m;
-  if (msb > 52) {
-    const int sh = msb - 52;
-    unsigned long long q = a >> sh, rem = a & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
-    if (rem > half || (rem == half && (q & 1ULL))) {
-      ++q;
-      if (q >> 53) { q >>= 1; ++ex; }
-    }
-    m = q;
-  } else {
-    m = a << (52 - msb);
-  }
+  const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ULL;
+  const unsigned long long a = x < 0 ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+  const int lz = __clzll((long long)a);
+  const unsigned long long m = a << lz;                       // leading one at bit 63
+  // keep bits 63..11, rounded to nearest even: add 2^10 - 1 and the bit that becomes the last one
+  const unsigned long long r = m + (0x3FFULL + ((m >> 11) & 1ULL));
+  const int carry = r < m ? 1 : 0;                            // the rounding carried past bit 63
+  const unsigned long long mant = carry ? (1ULL << 52) : (r >> 11);   // 53 bits, leading one at 52
+  const int ex = 63 - lz + e2 + carry;                        // value = mant 2^(ex - 52)
   if (ex + 1023 <= 0) return 0.0;
   if (ex + 1023 >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ULL));
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+  // the leading one of mant adds the last unit of the biased exponent
+  return __longlong_as_double((long long)(sgn | (mant + ((unsigned long long)(ex + 1022) << 52))));
 }
 
 // round(f 2^sc) for the FP32 value with bits fb (|f 2^sc| < 2^62), by integer operations (a
