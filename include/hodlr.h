@@ -281,7 +281,8 @@ int hodlr_dgemm_slices(int M, int N, int K, int batch, const double* A, long lon
  * enable != 0 the context's later builds and evaluations (HODLR_MIXED_BF16 contexts; not
  * inside a captured graph) time, at the first occurrence of each digit-slice product shape,
  * every candidate plan: the product from slice planes in the workspace (128 x 96 tiles, or for
- * K > 128 also 128 x 48 tiles with two CTAs per SM), and where the shape allows, the fused kernels
+ * K > 128 also 128 x 48 tiles with two CTAs per SM or in a persistent warp-specialised kernel),
+ * and where the shape allows, the fused kernels
  * with either tile (64 x 80 or 128 x 48 for long-K A^T B) and one or four times the default
  * chunks of K per CTA.  Each candidate runs once to warm up and twice
  * timed (CUDA events on the context's stream) into a scratch C carved from the slice
@@ -298,8 +299,8 @@ int hodlr_autotune_table(int64_t* out, int cap, int* n_out);
 int hodlr_autotune_clear(void);
 
 /* Kernel plan of the following hodlr_dgemm_slices calls on the calling thread (tests and shape
- * studies): path 0 slice planes (tile 0: 128 x 96, tile 1: 128 x 48 with two CTAs per SM, for
- * K > 128), path 1 the fused kernels where the shape allows them (tile 0 default, tile 1 the
+ * studies): path 0 slice planes (tile 0: 128 x 96, tile 1: 128 x 48 with two CTAs per SM, tile 2:
+ * persistent warp-specialised 128 x 48, the last two for K > 128), path 1 the fused kernels where the shape allows them (tile 0 default, tile 1 the
  * 128 x 48 long-K tile; cprx: chunks of K per CTA times the default), path -1 automatic (the
  * default plan, or the autotuner's).  A plan a shape does not allow falls back to slice planes
  * with the default tile.  HODLR_EINVAL for other values.  */

@@ -539,28 +539,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 3 - ST)
 // Every wait is bounded; a role whose wait gives up raises an abort flag that stops the others,
 // records HODLR_ETIMEOUT, waits (bounded) for what it issued and lets the CTA free its TMEM.
 constexpr int WS_BN = 32, WS_NST = 3, WS_THREADS = 320;
-constexpr int WS_STAGE = OZ_S * (OZ_PLANE_A + WS_BN * OZ_BK * 2);   // 70 KB
-constexpr int WS_SMEM = WS_NST * WS_STAGE + 1024 + 256;
+template <int BN, int NST> struct WsTile {
+  static constexpr int PLANE_B = BN * OZ_BK * 2;
+  static constexpr int STAGE = OZ_S * (OZ_PLANE_A + PLANE_B);   // 70 KB (BN 32), 77 KB (BN 48)
+  static constexpr int SMEM = NST * STAGE + 1024 + 256;
+  static constexpr int EPC = BN / 2;                             // epilogue columns per warp
+};
+constexpr int WS_SMEM = WsTile<WS_BN, WS_NST>::SMEM;
 
 __device__ __forceinline__ void oz_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(bar)) : "memory");
 }
 
+// Work items (product b, K chunk sp, row tile, column tile), column tile fastest; an item covers
+// one 512-long chunk of K (at most 16 slices) and writes C (one chunk) or its split-K partial.
+// Tiles 128 x 32 with three stages serve K <= 128; tiles 128 x 48 with two stages serve longer K
+// (the accumulator set of the next item is filled while the epilogue drains this one).
+template <int BN, int NST>
 __global__ void __launch_bounds__(WS_THREADS, 1)
     oz_mma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      const OzParams p, int ntm, int ntn, int ntiles) {
+  using TL = WsTile<BN, NST>;
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + WS_NST * WS_STAGE);
-  uint64_t* empty = full + WS_NST;
-  uint64_t* accf = empty + WS_NST;
+  uint64_t* full = (uint64_t*)(sm + NST * TL::STAGE);
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;
   uint64_t* acce = accf + 2;
   volatile int* abort_flag = (volatile int*)(acce + 2);
   uint32_t* tslot = (uint32_t*)(acce + 2) + 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nk = p.Kp / OZ_BK;                    // 1..4 slices, one K chunk
   if (tid == 0) {
-    for (int s = 0; s < WS_NST; ++s) {
+    for (int s = 0; s < NST; ++s) {
       oz_mbar_init(&full[s], 1);
       oz_mbar_init(&empty[s], 1);
     }
@@ -579,34 +589,39 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   __syncthreads();
   oz_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(WS_BN >> 3) << 17) |
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(OZ_BM >> 4) << 24);
-  auto planeA = [&](int s, int q) { return sm + s * WS_STAGE + q * OZ_PLANE_A; };
-  auto planeB = [&](int s, int q) { return sm + s * WS_STAGE + OZ_S * OZ_PLANE_A + q * (WS_BN * OZ_BK * 2); };
-  auto decode = [&](int t, int& b, int& m0, int& n0) {
+  auto planeA = [&](int s, int q) { return sm + s * TL::STAGE + q * OZ_PLANE_A; };
+  auto planeB = [&](int s, int q) { return sm + s * TL::STAGE + OZ_S * OZ_PLANE_A + q * TL::PLANE_B; };
+  auto decode = [&](int t, int& b, int& m0, int& n0, int& sp) {
     const int tn = t % ntn, r = t / ntn;
     m0 = (r % ntm) * OZ_BM;
-    n0 = tn * WS_BN;
-    b = r / ntm;
+    n0 = tn * BN;
+    const int r2 = r / ntm;
+    sp = r2 % p.nsplit;
+    b = r2 / p.nsplit;
   };
+  auto slices = [&](int sp) { return min(OZ_KC / OZ_BK, (p.Kp - sp * OZ_KC) / OZ_BK); };
   int issued = 0, committed = 0;   // producer / MMA progress (slices), for the drain after an abort
   if (warp == 8) {
     if (lane == 0) {
       // ---------------- producer
       int it = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-        int b, m0, n0;
-        decode(t, b, m0, n0);
+        int b, m0, n0, sp;
+        decode(t, b, m0, n0, sp);
         const int bA = p.nbA == 1 ? 0 : b;
         const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
+        const int nk = slices(sp);
         for (int kt = 0; kt < nk; ++kt, ++it) {
-          const int s = it % WS_NST, u = it / WS_NST;
+          const int s = it % NST, u = it / NST;
           if (u > 0 && !oz_wait(&empty[s], (u - 1) & 1)) { *abort_flag = 1; break; }
-          oz_expect_tx(&full[s], WS_STAGE);
+          oz_expect_tx(&full[s], TL::STAGE);
+          const int kx = (sp * (OZ_KC / OZ_BK) + kt) * OZ_BK;
 #pragma unroll
           for (int q = 0; q < OZ_S; ++q) {
-            oz_tma3(planeA(s, q), &mapA, kt * OZ_BK, m0, q * p.nbA + bA, &full[s]);
-            oz_tma3(planeB(s, q), &mapB, kt * OZ_BK, n0, q * p.nbB + bB, &full[s]);
+            oz_tma3(planeA(s, q), &mapA, kx, m0, q * p.nbA + bA, &full[s]);
+            oz_tma3(planeB(s, q), &mapB, kx, n0, q * p.nbB + bB, &full[s]);
           }
           issued = it + 1;
         }
@@ -620,10 +635,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         const int a = j & 1;
         if (j >= 2 && !oz_wait(&acce[a], ((j >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         oz_fence_after();
+        int b, m0, n0, sp;
+        decode(t, b, m0, n0, sp);
+        const int nk = slices(sp);
         bool ok = true;
         for (int kt = 0; kt < nk; ++kt, ++it) {
-          const int s = it % WS_NST;
-          if (!oz_wait(&full[s], (it / WS_NST) & 1)) { ok = false; break; }
+          const int s = it % NST;
+          if (!oz_wait(&full[s], (it / NST) & 1)) { ok = false; break; }
           oz_fence_after();
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
@@ -633,7 +651,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
               for (int pb = 0; pb < OZ_S - pa; ++pb) {
                 const int tt = pa + pb, g = tt < OZ_NACC - 1 ? tt : OZ_NACC - 1;
                 const bool first = kt == 0 && kk == 0 && pa == 0 && (g < OZ_NACC - 1 || tt == OZ_NACC - 1);
-                oz_mma(tmem + (uint32_t)(256 * a + g * WS_BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
+                oz_mma(tmem + (uint32_t)(256 * a + g * BN), oz_desc(oz_smem(planeA(s, pa)) + 32 * kk),
                        oz_desc(oz_smem(planeB(s, pb)) + 32 * kk), idesc, first ? 0u : 1u);
               }
             }
@@ -646,32 +664,34 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue
+    // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) .., columns EPC (w / 4) ..
+    constexpr int EPC = TL::EPC;
     const int wq = warp & 3, wh = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * wq) << 16;
     int j = 0;
-    for (int t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++j) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      if (__any_sync(0xffffffffu, *abort_flag)) break;
       const int a = j & 1;
       bool ok = oz_wait(&accf[a], (j >> 1) & 1);
       if (!__all_sync(0xffffffffu, ok)) { *abort_flag = 1; break; }
       oz_fence_after();
-      int b, m0, n0;
-      decode(t, b, m0, n0);
+      int b, m0, n0, sp;
+      decode(t, b, m0, n0, sp);
       const int bA = p.nbA == 1 ? 0 : b;
       const int bB = p.nbB == 1 ? 0 : (p.bmap == BMAP_XOR1 ? (b ^ 1) : (p.bmap == BMAP_SHR1 ? (b >> 1) : b));
       const int row = m0 + 32 * wq + lane;
-      const int c0 = n0 + 16 * wh;
+      const int c0 = n0 + EPC * wh;
       const int ea = row < p.M ? p.exA[(size_t)bA * p.M + row] : -2000;
-      double v[16];
+      double v[EPC];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < EPC / 8; ++h) {
         uint32_t ra[8], rb[8], rc[8], rd[8], rt[8];
-        const uint32_t base = tmem + lanes + (uint32_t)(256 * a + 16 * wh + 8 * h);
+        const uint32_t base = tmem + lanes + (uint32_t)(256 * a + EPC * wh + 8 * h);
         oz_ld8(base, ra);
-        oz_ld8(base + (uint32_t)WS_BN, rb);
-        oz_ld8(base + (uint32_t)(2 * WS_BN), rc);
-        oz_ld8(base + (uint32_t)(3 * WS_BN), rd);
-        oz_ld8(base + (uint32_t)(4 * WS_BN), rt);
+        oz_ld8(base + (uint32_t)BN, rb);
+        oz_ld8(base + (uint32_t)(2 * BN), rc);
+        oz_ld8(base + (uint32_t)(3 * BN), rd);
+        oz_ld8(base + (uint32_t)(4 * BN), rt);
         oz_ld_wait();
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -680,21 +700,28 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           v[8 * h + q] = oz_combine(ra[q], rb[q], rc[q], rd[q], rt[q], ea, eb);
         }
       }
-      // the accumulator set is free for the tile after next
+      // the accumulator set is free for the item after next
       oz_fence_before();
       __syncwarp();
       if (lane == 0) oz_arrive(&acce[a]);
       if (row < p.M) {
-        double* c = p.C + (size_t)b * p.sC + row;
-        double cv[16];
-        if (p.bmode != 0) {
+        if (p.nsplit > 1) {
+          double* pp = p.part + ((size_t)b * p.nsplit + sp) * ((size_t)p.M * p.N) + row;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) cv[q] = c0 + q < p.N ? c[(size_t)(c0 + q) * p.ldc] : 0.0;
-        }
+          for (int q = 0; q < EPC; ++q)
+            if (c0 + q < p.N) pp[(size_t)(c0 + q) * p.M] = v[q];
+        } else {
+          double* c = p.C + (size_t)b * p.sC + row;
+          double cv[EPC];
+          if (p.bmode != 0) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          if (c0 + q >= p.N) continue;
-          c[(size_t)(c0 + q) * p.ldc] = oz_out(v[q], cv[q], p.amode, p.bmode, p.alpha, p.beta);
+            for (int q = 0; q < EPC; ++q) cv[q] = c0 + q < p.N ? c[(size_t)(c0 + q) * p.ldc] : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < EPC; ++q) {
+            if (c0 + q >= p.N) continue;
+            c[(size_t)(c0 + q) * p.ldc] = oz_out(v[q], cv[q], p.amode, p.bmode, p.alpha, p.beta);
+          }
         }
       }
     }
@@ -704,9 +731,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     // wait (bounded) for the copies and products already issued before the TMEM is freed
     if (tid == 0) atomicExch(&g_oz_status, HODLR_ETIMEOUT);
     if (warp == 8 && lane == 0)
-      for (int it = issued - 1; it >= 0 && it >= issued - WS_NST; --it) oz_wait(&full[it % WS_NST], (it / WS_NST) & 1);
+      for (int it = issued - 1; it >= 0 && it >= issued - NST; --it) oz_wait(&full[it % NST], (it / NST) & 1);
     if (warp == 9 && lane == 0 && committed > 0)
-      oz_wait(&empty[(committed - 1) % WS_NST], ((committed - 1) / WS_NST) & 1);
+      oz_wait(&empty[(committed - 1) % NST], ((committed - 1) / NST) & 1);
   }
   oz_fence_before();
   __syncthreads();
@@ -1529,8 +1556,9 @@ bool oz_gemm(const GemmArgs& g, Scratch split, cudaStream_t st) {
 
 // the products from slice planes in the workspace (oz_mma_kernel / oz_mma_ws_kernel)
 // tile 0: 128 x 96 tiles, two stages, one CTA per SM; tile 1: 128 x 48 tiles, one stage, two CTAs
-// per SM (one CTA's epilogue overlaps the other's loads and products); K <= 128 always takes the
-// persistent 128 x 32 kernel
+// per SM (one CTA's epilogue overlaps the other's loads and products); tile 2: the persistent
+// warp-specialised kernel over 128 x 48 tiles and K chunks; K <= 128 always takes the persistent
+// 128 x 32 kernel
 static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st, int tile = 0) {
   const Scratch w = g_oz_cfg.work;
   const int Kp = ((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK;
@@ -1577,16 +1605,21 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st, int til
   // short K (one to four 32-wide slices): the persistent warp-specialised kernel over 128 x 32 tiles
   const bool narrow = Kp <= 4 * OZ_BK;
   const bool half = !narrow && tile == 1;
+  const bool ws48 = !narrow && tile == 2;   // persistent warp-specialised 128 x 48 tiles
   using Wide = OzTile<OZ_BN, 2>;
   using Half = OzTile<OZ_BN / 2, 1>;
-  const int bn = narrow ? WS_BN : (half ? OZ_BN / 2 : OZ_BN);
+  using Ws48 = WsTile<48, 2>;
+  const int bn = narrow ? WS_BN : (half || ws48 ? OZ_BN / 2 : OZ_BN);
   static int num_sms = 0;
   if (!num_sms) {
     int dev = 0;
     HODLR_CUDA(cudaGetDevice(&dev));
     HODLR_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  if (narrow) HODLR_CUDA(cudaFuncSetAttribute(oz_mma_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM));
+  if (narrow)
+    HODLR_CUDA(cudaFuncSetAttribute(oz_mma_ws_kernel<WS_BN, WS_NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM));
+  else if (ws48)
+    HODLR_CUDA(cudaFuncSetAttribute(oz_mma_ws_kernel<48, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Ws48::SMEM));
   else if (half)
     HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<OZ_BN / 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Half::SMEM));
   else HODLR_CUDA(cudaFuncSetAttribute(oz_mma_kernel<OZ_BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide::SMEM));
@@ -1635,12 +1668,13 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st, int til
       dim3 grid(p.nfast ? cdiv(nc, bn) : cdiv(g.M, OZ_BM), p.nfast ? cdiv(g.M, OZ_BM) : cdiv(nc, bn), nb * nsplit);
       const bool prof = g_prof.on && g_prof.n < g_prof.cap;
       if (prof) cudaEventRecord(g_prof.ev[2 * g_prof.n], st);
-      if (narrow) {
-        const int ntm = cdiv(g.M, OZ_BM), ntn = cdiv(nc, WS_BN);
-        const long long ntiles = (long long)ntm * ntn * nb;
+      if (narrow || ws48) {
+        const int ntm = cdiv(g.M, OZ_BM), ntn = cdiv(nc, bn);
+        const long long ntiles = (long long)ntm * ntn * nb * nsplit;
         if (ntiles > 0x7fffffffLL) throw Error(HODLR_EINVAL, "oz_gemm: too many tiles");
         const int ctas = (int)std::min<long long>(ntiles, num_sms);
-        oz_mma_ws_kernel<<<ctas, WS_THREADS, WS_SMEM, st>>>(ma, mb, p, ntm, ntn, (int)ntiles);
+        if (narrow) oz_mma_ws_kernel<WS_BN, WS_NST><<<ctas, WS_THREADS, WS_SMEM, st>>>(ma, mb, p, ntm, ntn, (int)ntiles);
+        else oz_mma_ws_kernel<48, 2><<<ctas, WS_THREADS, Ws48::SMEM, st>>>(ma, mb, p, ntm, ntn, (int)ntiles);
         check_launch("oz_mma_ws_kernel");
       } else {
         if (half) oz_mma_kernel<OZ_BN / 2, 1><<<grid, OZ_THREADS, Half::SMEM, st>>>(ma, mb, p);
@@ -1669,7 +1703,7 @@ static bool oz_sliced(const GemmArgs& g, Scratch split, cudaStream_t st, int til
 
 // ---------------------------------------------------------------- tile autotuner
 // A product runs either from slice planes (path 0; tile 0: 128 x 96, tile 1: 128 x 48 with two
-// CTAs per SM) or fused (path 1; tile 0: 64 x 80 for M <= 64 else 128 x 48, tile 1: 128 x 48;
+// CTAs per SM, tile 2: persistent warp-specialised 128 x 48) or fused (path 1; tile 0: 64 x 80 for M <= 64 else 128 x 48, tile 1: 128 x 48;
 // cprx: chunks of K per CTA times the default).  The default
 // plan is the fused path where the shape allows it.  A context with tuning on times, on the
 // first occurrence of a shape, every candidate plan once (after a warm-up run, CUDA events on
@@ -1698,7 +1732,10 @@ static bool oz_run(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan pl)
 }
 static OzPlan oz_tune(const GemmArgs& g, Scratch split, cudaStream_t st, OzPlan def) {
   std::vector<OzPlan> cand{{0, 0, 1}};
-  if (((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK > 4 * OZ_BK) cand.push_back({0, 1, 1});   // 128 x 48 tiles
+  if (((g.K + OZ_BK - 1) / OZ_BK) * OZ_BK > 4 * OZ_BK) {   // 128 x 48 tiles: two CTAs per SM, or persistent
+    cand.push_back({0, 1, 1});
+    cand.push_back({0, 2, 1});
+  }
   const int kind = oz_fused_kind(g);
   if (kind == 1) {
     cand.push_back({1, 0, 1});
@@ -1813,7 +1850,7 @@ int oz_status_take(cudaStream_t st) {
 using namespace hodlr;
 
 extern "C" int hodlr_dgemm_slices_plan(int path, int tile, int cprx) {
-  if (path < -1 || path > 1 || tile < 0 || tile > 1 || cprx < 1) return HODLR_EINVAL;
+  if (path < -1 || path > 1 || tile < 0 || tile > (path == 0 ? 2 : 1) || cprx < 1) return HODLR_EINVAL;
   oz_force_plan(path, tile, cprx);
   return HODLR_OK;
 }

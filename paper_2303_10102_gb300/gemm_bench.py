@@ -1,6 +1,6 @@
 """Shape study of the FP64-class digit-slice product (hodlr_dgemm_slices) on one GPU.
 
-    python -m paper_2303_10102_gb300.gemm_bench --shape M,N,K,batch,tA,tB [--shape ...] [--iters I]
+    python -m paper_2303_10102_gb300.gemm_bench --shape M,N,K,batch,tA,tB [--shape ...] [--iters I] [--plan P,T,C]
 
 For each shape the product C = A B (+ C when --beta 1) of random FP64 operands runs `iters` times
 after one warm-up call, timed with CUDA events on the library's stream around the whole call
@@ -32,8 +32,12 @@ def main(argv=None):
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--work-mb", type=int, default=2048)
     ap.add_argument("--hbm-gbs", type=float, default=None, help="copy bandwidth for the HBM fraction")
+    ap.add_argument("--plan", default=None, help="path,tile,cprx (hodlr_dgemm_slices_plan); default automatic")
     args = ap.parse_args(argv)
     lib = plib.load()
+    if args.plan:
+        if lib.hodlr_dgemm_slices_plan(*(int(x) for x in args.plan.split(","))) != 0:
+            raise ValueError(f"bad plan {args.plan}")
     dev = "cuda:0"
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()

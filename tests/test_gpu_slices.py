@@ -242,9 +242,10 @@ def test_fused_long_k_scaled_operands_ragged_and_batched():
             assert np.all(np.abs(got[b] - As[b] @ pick(b)) <= 1.5 * _bound(As[b], pick(b))), (bmap, b)
 
 
-@pytest.mark.parametrize("plan", [(0, 0, 1), (0, 1, 1), (1, 0, 1), (1, 1, 1), (1, 0, 4)])
+@pytest.mark.parametrize("plan", [(0, 0, 1), (0, 1, 1), (0, 2, 1), (1, 0, 1), (1, 1, 1), (1, 0, 4)])
 def test_every_kernel_plan_is_exact_and_accurate(plan):
-    """Each plan the autotuner can choose (slice planes with 128 x 96 or 128 x 48 tiles, fused with
+    """Each plan the autotuner can choose (slice planes with 128 x 96, two-CTA 128 x 48 or persistent
+    warp-specialised 128 x 48 tiles, fused with
     either tile and more chunks per CTA), forced for this thread, on a long-K A^T B, a short-K A B
     and a general A B: integer operands bit-exact, scaled operands within the slicing bound."""
     from paper_2303_10102_gb300 import lib as plib
