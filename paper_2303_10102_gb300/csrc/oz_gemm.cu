@@ -551,7 +551,8 @@ __device__ __forceinline__ void oz_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(bar)) : "memory");
 }
 
-// Work items (product b, K chunk sp, row tile, column tile), column tile fastest; an item covers
+// Work items (product b, K chunk sp, row tile, column tile), the tiles of the smaller operand
+// fastest; an item covers
 // one 512-long chunk of K (at most 16 slices) and writes C (one chunk) or its split-K partial.
 // Tiles 128 x 32 with three stages serve K <= 128; tiles 128 x 48 with two stages serve longer K
 // (the accumulator set of the next item is filled while the epilogue drains this one).
@@ -593,11 +594,21 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                          ((uint32_t)(OZ_BM >> 4) << 24);
   auto planeA = [&](int s, int q) { return sm + s * TL::STAGE + q * OZ_PLANE_A; };
   auto planeB = [&](int s, int q) { return sm + s * TL::STAGE + OZ_S * OZ_PLANE_A + q * TL::PLANE_B; };
+  // the larger operand's tile is shared by the items that run together (p.nfast: column tiles
+  // fastest, A shared; else row tiles fastest, B shared)
   auto decode = [&](int t, int& b, int& m0, int& n0, int& sp) {
-    const int tn = t % ntn, r = t / ntn;
-    m0 = (r % ntm) * OZ_BM;
+    int tm, tn, r2;
+    if (p.nfast) {
+      tn = t % ntn;
+      tm = (t / ntn) % ntm;
+      r2 = t / ntn / ntm;
+    } else {
+      tm = t % ntm;
+      tn = (t / ntm) % ntn;
+      r2 = t / ntm / ntn;
+    }
+    m0 = tm * OZ_BM;
     n0 = tn * BN;
-    const int r2 = r / ntm;
     sp = r2 % p.nsplit;
     b = r2 / p.nsplit;
   };
