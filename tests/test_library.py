@@ -160,3 +160,13 @@ def test_autotune_table_and_argument_errors(so_path):
     assert lib.hodlr_autotune_table(None, 0, None) == -1
     assert lib.hodlr_autotune(None, 1) == -1
     assert plib.autotune_table() == []
+
+
+def test_slice_plan_argument_errors(so_path):
+    """hodlr_dgemm_slices_plan validates its plan on the host (no device work)."""
+    lib = plib.load()
+    for bad in [(2, 0, 1), (-2, 0, 1), (0, 3, 1), (1, 2, 1), (1, 0, 0)]:
+        assert lib.hodlr_dgemm_slices_plan(*bad) == -1, bad
+    for good in [(0, 0, 1), (0, 2, 1), (1, 1, 4), (-1, 0, 1)]:
+        assert lib.hodlr_dgemm_slices_plan(*good) == 0, good
+    assert lib.hodlr_dgemm_slices_plan(-1, 0, 1) == 0
